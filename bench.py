@@ -1,0 +1,278 @@
+"""Benchmark of the thermal multiphase LB lattice update on GB300.
+
+Workload: D3Q19 thermal pool boiling, 384 x 384 x 256 (37,748,736 nodes),
+bounce-back walls on z with the bottom wall at T = 0.95 and an adiabatic top,
+liquid layer 64 nodes deep at T = 0.8 under its saturated vapour, gravity
+-1e-5 z via EDM, +-1e-4 seeded density noise, FP32 populations.  One step is
+one lattice update of every node (moments, EOS, force, finite-difference
+energy change, collision of both population sets, streaming, walls).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  value = MLUPS over all ranks (each rank runs
+its own replica of the workload: weak scaling).  The populations (11.5 GB of
+reads and writes per step) are far larger than L2, so no flush is needed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY, NZ = 384, 384, 256
+WORKLOAD = "D3Q19 thermal pool boiling 384x384x256, walls on z (bottom T=0.95 fixed, top adiabatic), " \
+           "liquid 64 deep at T=0.8, g=-1e-5 z, FP32"
+METRIC = "MLUPS (thermal D3Q19 FP32, pool boiling 384x384x256)"
+FALLBACK_HBM_GBS = 6800.0
+PARAMS = dict(lattice=19, nx=NX, ny=NY, nz=NZ, wall=1, T_fixed_lo=1, T_lo=0.95, gravity=(0.0, 0.0, -1e-5),
+              kappa=0.01, A=-0.152, tau=1.0, tau_E=1.0, c_v=1.5, lambda_=0.05)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _fields():
+    from paper_1705_10045_gb300 import workloads as W
+    return W.pool_boiling_3d(nx=NX, ny=NY, nz=NZ, T=0.8, depth=64, noise=1e-4, seed=3)
+
+
+def _peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in d:
+                    v = d[key]
+                    v = v.get("value", v) if isinstance(v, dict) else v
+                    return float(v), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(budget_s: float = 15.0):
+    """The FP64 C oracle, single-threaded, on a bounded sample of the workload:
+    a 96 x 96 x 64 box of the same structure (walls, heated floor, liquid 16
+    deep, gravity), stepped until about `budget_s` seconds of CPU time."""
+    import oracle
+    from paper_1705_10045_gb300 import workloads as W
+    nx, ny, nz = 96, 96, 64
+    f = W.pool_boiling_3d(nx=nx, ny=ny, nz=nz, T=0.8, depth=16, noise=1e-4, seed=3)
+    p = oracle.Params(Q=19, nx=nx, ny=ny, nz=nz, wall=True, T_fixed_lo=True, T_lo=0.95, g=(0.0, 0.0, -1e-5))
+    s = oracle.State(p, f.rho, f.u, p.c_v * f.T)
+    t0 = time.perf_counter()
+    s.step(1)
+    one = time.perf_counter() - t0
+    n = max(1, int(budget_s / max(one, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    s.step(n)
+    dt = time.perf_counter() - t0
+    return {"value": nx * ny * nz * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 C oracle, 1 thread, D3Q19 {nx}x{ny}x{nz} box of the same structure "
+                      f"(walls, heated floor, liquid 16 deep, gravity), {n} steps in {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, each step one oracle
+    step of a 64 x 64 x 64 box of the workload's structure."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1705_10045_gb300 import workloads as W
+    n = 64
+    f = W.pool_boiling_3d(nx=n, ny=n, nz=n, T=0.8, depth=16, noise=1e-4, seed=3)
+    p = oracle.Params(Q=19, nx=n, ny=n, nz=n, wall=True, T_fixed_lo=True, T_lo=0.95, g=(0.0, 0.0, -1e-5))
+    s = oracle.State(p, f.rho, f.u, p.c_v * f.T)
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = n ** 3 * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{n}^3 box of the same structure"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"FP64 C oracle, 1 thread, {n}^3 box, {args.steps} steps"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    from paper_1705_10045_gb300 import lbm
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+
+    f = _fields()
+    nn = NX * NY * NZ
+    c_v = PARAMS["c_v"]
+    # pinned host copies of the inputs (used by the end-to-end leg)
+    rho_h = torch.from_numpy(f.rho).pin_memory()
+    u_h = torch.from_numpy(np.ascontiguousarray(f.u)).pin_memory()
+    eps_h = torch.from_numpy(c_v * f.T).pin_memory()
+    del f
+
+    sim = lbm.Lbm(storage=lbm.LBM_STORE_FP32, device=dev, stream=stream.cuda_stream, **PARAMS)
+    sim.init(rho_h, u_h, eps_h)
+    launches = lbm.lbm_launches_per_step(sim.h)
+
+    # warm-up, then per-kernel event timing of a few steps for the roofline
+    sim.step(args.warmup)
+    prof = lbm.lbm_profile_step(sim.h, max(3, min(20, args.steps // 10)))
+    torch.cuda.synchronize()
+
+    # timed region: K steps between events on the library's stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    diag = sim.diagnostics()
+
+    # end to end through the C-ABI with host buffers: init from pinned host
+    # fields, K steps, moments back to pinned host buffers
+    out = {k: torch.empty(shape, dtype=torch.float64).pin_memory()
+           for k, shape in (("rho", (NZ, NY, NX)), ("u", (3, NZ, NY, NX)), ("T", (NZ, NY, NX)),
+                            ("P", (NZ, NY, NX)))}
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    sim.init(rho_h, u_h, eps_h)
+    sim.step(args.steps)
+    lbm.lbm_moments(sim.h, out["rho"], out["u"], out["T"], out["P"])
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = (rho_h.numel() + u_h.numel() + eps_h.numel()) * 8
+    d2h = sum(v.numel() for v in out.values()) * 8
+    sim.close()
+
+    if rank == 0:
+        peak, peak_kind = _peak()
+        top = max(prof, key=prof.get)
+        # algorithmic bytes of the dominant kernel per node: the collide kernel
+        # reads and writes both FP32 population sets (4 Q s = 304 B) and reads
+        # the 8 field values it needs of its own node (32 B)
+        algo_bytes = {"collide_kernel": 4 * 19 * 4 + 8 * 4}.get(top, 4 * 19 * 4)
+        achieved = algo_bytes * nn / (prof[top] * 1e-3) / 1e9
+        value = nn * args.steps * ws / (ms * 1e-3) / 1e6
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": nn, "l2": "inputs larger than L2 (11.5 GB of population "
+                       "traffic per step vs 129 MB L2), no flush", "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "algorithmic_bytes_per_node": algo_bytes, "kernel_ms": prof,
+                         "step_bytes_per_node": 4 * 19 * 4,
+                         "step_frac": 4 * 19 * 4 * nn / (ms / args.steps * 1e-3) / 1e9 / peak},
+            "e2e": {"value": nn * args.steps * ws / e2e_s / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
+            "gpu_launches": launches * args.steps,
+            "clocks": clk.summary(),
+            "diagnostics": {"mass": diag["mass"], "energy": diag["energy"], "clamps": diag["clamps"],
+                            "bad": diag["bad"]},
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * liblbm: GB300 (sm_103a) library for the per-time-step lattice update of the
+ * thermal multiphase lattice Boltzmann method of Kupershtokh, Medvedev and
+ * Gribanov, "Thermal lattice Boltzmann method for multiphase flows"
+ * (arXiv:1705.10045).
+ *
+ * One time step (lbm_step) does, for every node of a D2Q9 or D3Q19 lattice:
+ *   1. moments rho = sum N_k, rho u = sum c_k N_k (Eq. (hydro)), E = sum g_k,
+ *      T = E/(rho c_v) (Sec. 4);
+ *   2. van der Waals pressure p = kappa p~(rho, T), pseudopotential
+ *      U = p - rho theta, Phi = sqrt(-U) (Sec. 3, Eq. (force));
+ *   3. the mixed interparticle force of Sec. 3 (mixing parameter A, stencil
+ *      weights G_k, alpha) plus gravity, du = F dt/rho, u* = u + du/2
+ *      (Eq. (edm), Eq. (ustar));
+ *   4. the finite-difference energy change dE = -p div(u*) + div(lambda grad T)
+ *      (Sec. 4, Sec. 6.2);
+ *   5. BGK collision + EDM source for N (Eq. (lbe), Eq. (edm)) and, for the
+ *      energy populations g (Eq. (gk)), BGK + g dE/E + the energy pseudoforce
+ *      g^eq(E, u+du) - g^eq(E, u) (Sec. 4);
+ *   6. streaming to x + c_k, periodic, or halfway bounce-back at walls on the
+ *      last axis (y for D2Q9, z for D3Q19), optionally held at a fixed
+ *      temperature through the conduction term.
+ *
+ * Lattice units: h = dt = 1, theta = 1/3.  Velocity ordering: k = 0 rest,
+ * then nearest neighbours, then next-nearest, each direction followed by its
+ * opposite (D2Q9: +x -x +y -y (+x+y) (-x-y) (+x-y) (-x+y); D3Q19: +x -x +y -y
+ * +z -z, then the face diagonals (+x+y)(-x-y)(+x-y)(-x+y)(+x+z)(-x-z)(+x-z)
+ * (-x+z)(+y+z)(-y-z)(+y-z)(-y+z)).
+ *
+ * Field layout for every array crossing this interface: structure of arrays,
+ * x fastest: a scalar field is nx*ny*nz doubles indexed (z*ny + y)*nx + x
+ * (nz = 1 for D2Q9); a vector field is d such planes (x component first).
+ *
+ * Errors: every call returns LBM_OK (0) or a negative LBM_ERR_* code and
+ * leaves a message for lbm_last_error() (thread-local).  Device-side
+ * problems (U >= 0 clamped, non-finite or non-positive density or energy)
+ * are counted on the device and reported as LBM_ERR_NONPHYSICAL by the
+ * next synchronising call (lbm_moments, lbm_diagnostics, lbm_sync,
+ * lbm_get_state).  Calls on one handle are not thread-safe.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_ERR_INVALID_ARG (-1)
+#define LBM_ERR_UNSTABLE_PARAMS (-2)
+#define LBM_ERR_OOM (-3)
+#define LBM_ERR_CUDA (-4)
+#define LBM_ERR_NONPHYSICAL (-5)
+
+#define LBM_D2Q9 9
+#define LBM_D3Q19 19
+
+/* storage (and arithmetic) of the population sets */
+#define LBM_STORE_FP64 0 /* FP64 storage, FP64 arithmetic */
+#define LBM_STORE_FP32 1 /* FP32 storage, FP32 arithmetic */
+#define LBM_STORE_FP16 2 /* FP16 storage of N_k - w_k rho_ref and g_k - w_k E_ref, FP32 arithmetic */
+
+/* how a time step is launched: one fused kernel that marches CTA tiles along
+ * the last lattice axis, or three kernels (moments/Phi, force, collide+stream)
+ * with the fields in device memory; both compute the same step */
+#define LBM_STEP_FUSED 0
+#define LBM_STEP_THREE_LAUNCH 1
+
+/* where a caller buffer lives */
+#define LBM_MEM_HOST 0
+#define LBM_MEM_DEVICE 1
+
+typedef struct lbm_handle lbm_handle;
+
+/* Parameters of one simulation domain.  Citations give the passage that
+ * defines each quantity. */
+typedef struct lbm_params {
+    int lattice;          /* LBM_D2Q9 or LBM_D3Q19 (Sec. 2) */
+    int nx, ny, nz;       /* lattice size; nz must be 1 for D2Q9 */
+    double kappa;         /* lattice pressure scale: p = kappa p~(rho, T), reduced vdW
+                             p~ = 8 rho T/(3 - rho) - 3 rho^2 (Sec. 3) */
+    double A;             /* force mixing parameter (Sec. 3; -0.152 for vdW) */
+    int barotropic;       /* nonzero: the EOS uses T0 instead of T (Sec. 4) */
+    double T0;
+    double tau;           /* relaxation time of N (Sec. 2), > 1/2 */
+    double tau_E;         /* relaxation time of g (Eq. (gk)), > 1/2 */
+    double c_v;           /* specific heat, E = rho c_v T (Sec. 4), > 0 */
+    int chi_mode;         /* 0: constant conductivity lambda; 1: lambda = rho c_v chi (Sec. 4) */
+    double lambda, chi;
+    double gravity[3];    /* body force per unit mass, added to F (Sec. 2: F is the total force) */
+    int wall;             /* last axis: 0 periodic, 1 bounce-back walls beyond both ends */
+    int T_fixed_lo, T_fixed_hi; /* per wall: 0 adiabatic, 1 held at T_lo / T_hi */
+    double T_lo, T_hi;
+    int pressure_work;    /* include -p div(u*) in dE (Sec. 4) */
+    int conduction;       /* include div(lambda grad T) in dE (Sec. 4) */
+    int pseudoforce;      /* include the energy pseudoforce (Sec. 4) */
+    int storage;          /* LBM_STORE_* */
+    double rho_ref, E_ref;/* shifts of the FP16 storage (ignored otherwise) */
+    int step_kernel;      /* LBM_STEP_FUSED (default) or LBM_STEP_THREE_LAUNCH */
+    void* stream;         /* cudaStream_t the library enqueues on (NULL: default stream) */
+    int device;           /* CUDA device ordinal */
+} lbm_params;
+
+/* Fill *p with defaults: D2Q9 64x64x1, kappa 0.01, A -0.152, tau = tau_E = 1,
+ * c_v 1.5, lambda 0.05, periodic, all physics switches on, FP32 storage,
+ * rho_ref 1, E_ref 1.2, default stream, device 0. */
+void lbm_default_params(lbm_params* p);
+
+/* Validate *p, run the pre-flight checks (tau, tau_E > 1/2; c_v > 0;
+ * kappa > 0; sizes >= 1 and nz == 1 for D2Q9; wall axis at least 2 nodes)
+ * and allocate all device state on p->device.  The library owns that state
+ * until lbm_destroy.  Errors: LBM_ERR_INVALID_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_create(const lbm_params* p, lbm_handle** out);
+
+/* Set the populations to equilibrium: N = N^eq(rho, u), g = g^eq(rho eps, u)
+ * (Eq. (feq)), where eps = c_v T is the specific internal energy and u is
+ * taken as the lattice velocity of Eq. (hydro).  rho, eps: one plane each;
+ * u: d planes.  mem says whether the three pointers are host or device
+ * memory; the library copies them and does not keep them.  Rejects
+ * rho <= 0, eps <= 0, non-finite values and U = p - rho theta >= 0
+ * (LBM_ERR_NONPHYSICAL), and nodes breaking the stability criteria
+ * (dp/drho)_T <= (h/dt)^2 + theta (Sec. 3) or chi dt/h^2 < 0.5/d (Sec. 6.1)
+ * (LBM_ERR_UNSTABLE_PARAMS); the checks run on the device.  Host input goes
+ * through a device staging buffer the handle keeps.  Resets the step
+ * counter.  Synchronising. */
+int lbm_init(lbm_handle* h, const double* rho, const double* u, const double* eps, int mem);
+
+/* Enqueue n time steps on the handle's stream (asynchronous, n >= 0). */
+int lbm_step(lbm_handle* h, int n);
+
+/* Output fields of the current state: rho, the physical velocity u*
+ * (Eq. (ustar), d planes), T = E/(rho c_v) and P = kappa p~(rho, T).  Any
+ * pointer may be NULL.  mem: host or device.  Synchronising; returns a
+ * latched device error if any. */
+int lbm_moments(lbm_handle* h, double* rho, double* u, double* T, double* P, int mem);
+
+/* Global sums of the current state, reduced in FP64 with Kahan compensation in
+ * a fixed order (bitwise reproducible): out[0] mass, out[1..3] momentum
+ * sum c_k N_k (x, y, z), out[4] internal energy, out[5] clamped nodes (U >= 0)
+ * and out[6] non-finite or non-positive nodes since the last lbm_init,
+ * out[7] steps taken since lbm_init.  Synchronising. */
+int lbm_diagnostics(lbm_handle* h, double out[8]);
+
+/* Size in bytes of the raw state for lbm_get_state / lbm_set_state: a
+ * 16-byte header (magic "LBM1", lattice, storage, step count) followed by the
+ * 2Q population planes (N then g) in the storage format. */
+size_t lbm_state_bytes(const lbm_handle* h);
+
+/* Copy the raw state out or in (checkpoint / resume; resuming is bitwise
+ * identical to not stopping).  buf is host or device memory of
+ * lbm_state_bytes bytes.  Synchronising. */
+int lbm_get_state(lbm_handle* h, void* buf, int mem);
+int lbm_set_state(lbm_handle* h, const void* buf, int mem);
+
+/* Wait for the handle's stream; returns a latched device error if any. */
+int lbm_sync(lbm_handle* h);
+
+/* Number of kernel launches one lbm_step(1) enqueues. */
+int lbm_launches_per_step(const lbm_handle* h);
+
+/* Advance n >= 1 steps like lbm_step, with a CUDA event pair around every
+ * launch on the handle's stream, and write the mean duration in ms of launch
+ * j of a step to ms[j] for j < min(cap, launches).  Returns the number of
+ * launches per step (> 0) or an LBM_ERR_* code.  Synchronising. */
+int lbm_profile_step(lbm_handle* h, int n, double* ms, int cap);
+
+/* Kernel name of launch j of a step ("" when out of range). */
+const char* lbm_launch_name(const lbm_handle* h, int j);
+
+/* Free all device state.  NULL is allowed. */
+void lbm_destroy(lbm_handle* h);
+
+/* Message of the last error on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,186 @@
+// Launch sequences of the liblbm back end for one lattice, for every storage
+// format.  Included once per lattice by lbm_d2q9.cu and lbm_d3q19.cu.
+//
+// A time step is either the fused single launch (fused_step_kernel, the
+// default) or the three-launch form fields -> force -> collide, kept as a
+// second, independently structured statement of the same step.
+#pragma once
+
+#include "fused.cuh"
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace lbm {
+
+template <typename R> KParams<R> make_kparams(const lbm_handle* h) {
+    const lbm_params& q = h->p;
+    KParams<R> k;
+    k.nx = q.nx; k.ny = q.ny; k.nz = q.nz; k.nn = h->nn;
+    k.kappa = (R)q.kappa; k.A = (R)q.A; k.T0 = (R)q.T0; k.barotropic = q.barotropic != 0;
+    k.omega = (R)(1.0 / q.tau); k.omega_E = (R)(1.0 / q.tau_E);
+    k.c_v = (R)q.c_v;
+    k.chi_mode = q.chi_mode != 0; k.lambda = (R)q.lambda; k.chi = (R)q.chi;
+    for (int a = 0; a < 3; ++a) k.g[a] = (R)q.gravity[a];
+    k.wall = q.wall != 0;
+    k.T_fixed_lo = q.T_fixed_lo != 0; k.T_fixed_hi = q.T_fixed_hi != 0;
+    k.T_lo = (R)q.T_lo; k.T_hi = (R)q.T_hi;
+    k.pressure_work = q.pressure_work != 0; k.conduction = q.conduction != 0; k.pseudoforce = q.pseudoforce != 0;
+    const bool shifted = q.storage == LBM_STORE_FP16;
+    k.rho_ref = shifted ? (R)q.rho_ref : R(0);
+    k.E_ref = shifted ? (R)q.E_ref : R(0);
+    return k;
+}
+
+inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// CTA tile of the fused kernel: 32 x 8 nodes of the xy plane for D3Q19, 64
+// nodes of a row for D2Q9.
+template <int Q> struct FusedTile;
+template <> struct FusedTile<9> { static constexpr int TX = 64, TY = 1; };
+template <> struct FusedTile<19> { static constexpr int TX = 32, TY = 8; };
+
+template <int Q, typename S, typename R> struct Impl {
+    static constexpr int TX = FusedTile<Q>::TX, TY = FusedTile<Q>::TY;
+
+    static int launches(const lbm_handle* h) { return h->p.step_kernel == LBM_STEP_THREE_LAUNCH ? 3 : 1; }
+
+    static MarchGeom geometry(const lbm_handle* h) {
+        MarchGeom G;
+        G.na = h->p.nx;
+        G.nb = Q == 9 ? 1 : h->p.ny;
+        G.nm = Q == 9 ? h->p.ny : h->p.nz;
+        // planes per CTA: enough CTAs for about four per SM on 152 SMs, and
+        // at least 8 planes so that the 4 extra ring planes stay a minority
+        const long long tiles = (long long)((G.na + TX - 1) / TX) * ((G.nb + TY - 1) / TY);
+        long long c = (G.nm * tiles + 607) / 608;
+        c = c < 8 ? 8 : (c > 64 ? 64 : c);
+        G.chunk = (int)(c > G.nm ? G.nm : c);
+        return G;
+    }
+
+    static void launch_fused(lbm_handle* h, const KParams<R>& kp) {
+        const MarchGeom G = geometry(h);
+        const size_t smem = FusedShape<TX, TY>::template smem_bytes<R>();
+        auto kern = fused_step_kernel<Q, S, R, TX, TY>;
+        if (!h->fused_ready) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            h->fused_ready = true;
+        }
+        const dim3 grid((G.na + TX - 1) / TX, (G.nb + TY - 1) / TY, (G.nm + G.chunk - 1) / G.chunk);
+        kern<<<grid, TX * TY, smem, h->stream>>>((const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], kp, G,
+                                                 (Counters*)h->cnt);
+        h->cur ^= 1;
+    }
+
+    // launch j of one time step; the last launch of a step swaps the buffers
+    static void launch(lbm_handle* h, const KParams<R>& kp, int j) {
+        if (h->p.step_kernel != LBM_STEP_THREE_LAUNCH) {
+            launch_fused(h, kp);
+            return;
+        }
+        const unsigned g = grid_for(h->nn, 256);
+        R* fld = (R*)h->fld;
+        const S* src = (const S*)h->pop[h->cur];
+        S* dst = (S*)h->pop[h->cur ^ 1];
+        if (j == 0) fields_kernel<Q, S, R><<<g, 256, 0, h->stream>>>(src, fld, kp, (Counters*)h->cnt, 1);
+        if (j == 1) force_kernel<Q, R><<<g, 256, 0, h->stream>>>(fld, kp);
+        if (j == 2) {
+            collide_kernel<Q, S, R><<<g, 256, 0, h->stream>>>(src, dst, fld, kp);
+            h->cur ^= 1;
+        }
+    }
+
+    static int step(lbm_handle* h, int n) {
+        const KParams<R> kp = make_kparams<R>(h);
+        const int L = launches(h);
+        for (int s = 0; s < n; ++s)
+            for (int j = 0; j < L; ++j) launch(h, kp, j);
+        return cuda_error(cudaGetLastError(), "lbm_step launch");
+    }
+
+    // n steps with an event pair around every launch; ms[j] = mean duration of launch j
+    static int profile(lbm_handle* h, int n, double* ms, int cap) {
+        const KParams<R> kp = make_kparams<R>(h);
+        const int L = launches(h);
+        cudaEvent_t ev[6];
+        for (int e = 0; e < 2 * L; ++e)
+            if (int rc = cuda_error(cudaEventCreate(&ev[e]), "event create")) return rc;
+        double acc[3] = {0.0, 0.0, 0.0};
+        int rc = LBM_OK;
+        for (int s = 0; s < n && !rc; ++s) {
+            for (int j = 0; j < L; ++j) {
+                cudaEventRecord(ev[2 * j], h->stream);
+                launch(h, kp, j);
+                cudaEventRecord(ev[2 * j + 1], h->stream);
+            }
+            rc = cuda_error(cudaEventSynchronize(ev[2 * L - 1]), "profile synchronize");
+            for (int j = 0; j < L && !rc; ++j) {
+                float t = 0.f;
+                rc = cuda_error(cudaEventElapsedTime(&t, ev[2 * j], ev[2 * j + 1]), "event time");
+                acc[j] += t;
+            }
+        }
+        for (int e = 0; e < 2 * L; ++e) cudaEventDestroy(ev[e]);
+        if (rc) return rc;
+        for (int j = 0; j < L && j < cap; ++j) ms[j] = n > 0 ? acc[j] / n : 0.0;
+        return L;
+    }
+
+    static int init(lbm_handle* h, const double* rho, const double* u, const double* eps) {
+        const KParams<R> kp = make_kparams<R>(h);
+        init_kernel<Q, S, R><<<grid_for(h->nn, 256), 256, 0, h->stream>>>((S*)h->pop[h->cur], rho, u, eps, kp,
+                                                                           (Counters*)h->cnt);
+        return cuda_error(cudaGetLastError(), "lbm_init launch");
+    }
+    static int moments(lbm_handle* h, double* rho, double* u, double* T, double* P) {
+        const KParams<R> kp = make_kparams<R>(h);
+        const unsigned g = grid_for(h->nn, 256);
+        R* fld = (R*)h->fld;
+        fields_kernel<Q, S, R><<<g, 256, 0, h->stream>>>((const S*)h->pop[h->cur], fld, kp, (Counters*)h->cnt, 0);
+        force_kernel<Q, R><<<g, 256, 0, h->stream>>>(fld, kp);
+        output_kernel<Q, R><<<g, 256, 0, h->stream>>>(fld, kp, rho, u, T, P);
+        return cuda_error(cudaGetLastError(), "lbm_moments launch");
+    }
+    static int reduce(lbm_handle* h, double* out_dev) {
+        const KParams<R> kp = make_kparams<R>(h);
+        reduce_kernel<Q, S, R><<<kReduceBlocks, kReduceThreads, 0, h->stream>>>((const S*)h->pop[h->cur], kp,
+                                                                                h->partials);
+        reduce_final_kernel<<<1, 32, 0, h->stream>>>(h->partials, kReduceBlocks, out_dev);
+        return cuda_error(cudaGetLastError(), "lbm_diagnostics launch");
+    }
+};
+
+#define LBM_DISPATCH(h, CALL)                                                   \
+    switch ((h)->p.storage) {                                                   \
+        case LBM_STORE_FP64: return Impl<Q, double, double>::CALL;              \
+        case LBM_STORE_FP32: return Impl<Q, float, float>::CALL;                \
+        case LBM_STORE_FP16: return Impl<Q, __half, float>::CALL;               \
+        default: set_error("unknown storage format"); return LBM_ERR_INVALID_ARG; \
+    }
+
+template <int Q> int Backend<Q>::step(lbm_handle* h, int n) { LBM_DISPATCH(h, step(h, n)); }
+template <int Q> int Backend<Q>::profile(lbm_handle* h, int n, double* ms, int cap) {
+    LBM_DISPATCH(h, profile(h, n, ms, cap));
+}
+template <int Q> const char* Backend<Q>::launch_name(const lbm_handle* h, int j) {
+    static const char* three[] = {"fields_kernel", "force_kernel", "collide_kernel"};
+    if (h->p.step_kernel == LBM_STEP_THREE_LAUNCH) return j >= 0 && j < 3 ? three[j] : "";
+    return j == 0 ? "fused_step_kernel" : "";
+}
+template <int Q> int Backend<Q>::launches(const lbm_handle* h) {
+    return h->p.step_kernel == LBM_STEP_THREE_LAUNCH ? 3 : 1;
+}
+template <int Q> int Backend<Q>::init(lbm_handle* h, const double* rho, const double* u, const double* eps) {
+    LBM_DISPATCH(h, init(h, rho, u, eps));
+}
+template <int Q> int Backend<Q>::moments(lbm_handle* h, double* rho, double* u, double* T, double* P) {
+    LBM_DISPATCH(h, moments(h, rho, u, T, P));
+}
+template <int Q> int Backend<Q>::reduce(lbm_handle* h, double* out_dev) { LBM_DISPATCH(h, reduce(h, out_dev)); }
+template <int Q> size_t Backend<Q>::field_bytes(int storage) {
+    return (size_t)F_COUNT * (storage == LBM_STORE_FP64 ? sizeof(double) : sizeof(float));
+}
+
+#undef LBM_DISPATCH
+
+}  // namespace lbm

@@ -1,0 +1,45 @@
+// Host-side state of one liblbm handle and the per-lattice back ends.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <string>
+
+#include "../../include/lbm.h"
+
+struct lbm_handle {
+    lbm_params p;
+    int Q = 0, D = 0;
+    long long nn = 0;
+    size_t elem = 0;            // bytes per stored population value
+    void* pop[2] = {nullptr, nullptr};   // ping-pong population buffers, 2Q planes each
+    int cur = 0;                // buffer holding the current state
+    void* fld = nullptr;        // field planes (arithmetic type)
+    void* cnt = nullptr;        // lbm::Counters on the device
+    double* partials = nullptr; // reduction scratch: block partials + 8 results
+    double* staging = nullptr;  // (D + 3) planes of doubles for host transfers, allocated on demand
+    unsigned long long reported_bad = 0;
+    long long steps = 0;
+    bool initialised = false;
+    bool fused_ready = false;   // shared-memory limit of the fused kernel raised
+    cudaStream_t stream = nullptr;
+};
+
+namespace lbm {
+
+// error reporting shared by the translation units
+void set_error(const std::string& msg);
+int cuda_error(cudaError_t e, const char* where);
+
+// per-lattice entry points, dispatched on the storage format inside
+template <int Q> struct Backend {
+    static int step(lbm_handle* h, int n);
+    static int profile(lbm_handle* h, int n, double* ms, int cap);   // returns launches per step
+    static const char* launch_name(const lbm_handle* h, int j);
+    static int launches(const lbm_handle* h);
+    static int init(lbm_handle* h, const double* rho, const double* u, const double* eps);   // device pointers
+    static int moments(lbm_handle* h, double* rho, double* u, double* T, double* P);       // device pointers
+    static int reduce(lbm_handle* h, double* out_dev);   // 5 sums into device memory
+    static size_t field_bytes(int storage);
+};
+
+}  // namespace lbm

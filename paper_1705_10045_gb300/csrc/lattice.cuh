@@ -1,0 +1,183 @@
+// Lattice constants, storage formats and per-node arithmetic of the thermal
+// multiphase LB step (Kupershtokh, Medvedev, Gribanov, arXiv:1705.10045).
+// Device-side building blocks shared by every kernel of liblbm.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cstdint>
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Velocity sets (Sec. 2).  k = 0 rest, then nearest neighbours, then
+// next-nearest; each direction is followed by its opposite.
+
+template <int Q> struct Vel;
+
+template <> struct Vel<9> {
+    static constexpr int D = 2;
+    __host__ __device__ static constexpr int cx(int k) {
+        constexpr int v[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+        return v[k];
+    }
+    __host__ __device__ static constexpr int cy(int k) {
+        constexpr int v[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+        return v[k];
+    }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    // weights w_k (Sec. 2): 4/9, 1/9, 1/36
+    __host__ __device__ static constexpr double w(int k) {
+        return k == 0 ? 4.0 / 9.0 : (k <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+    // force-stencil coefficients G_k and alpha (Sec. 3)
+    __host__ __device__ static constexpr double G(int k) {
+        return k == 0 ? 0.0 : (k <= 4 ? 1.0 : 0.25);
+    }
+    static constexpr double alpha = 1.5;
+};
+
+template <> struct Vel<19> {
+    static constexpr int D = 3;
+    __host__ __device__ static constexpr int cx(int k) {
+        constexpr int v[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+        return v[k];
+    }
+    __host__ __device__ static constexpr int cy(int k) {
+        constexpr int v[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+        return v[k];
+    }
+    __host__ __device__ static constexpr int cz(int k) {
+        constexpr int v[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+        return v[k];
+    }
+    // weights w_k (Sec. 2): 1/3, 1/18, 1/36
+    __host__ __device__ static constexpr double w(int k) {
+        return k == 0 ? 1.0 / 3.0 : (k <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+    // force-stencil coefficients G_k and alpha (Sec. 3)
+    __host__ __device__ static constexpr double G(int k) {
+        return k == 0 ? 0.0 : (k <= 6 ? 1.0 : 0.5);
+    }
+    static constexpr double alpha = 3.0;
+};
+
+__host__ __device__ constexpr int opposite(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+
+// ---------------------------------------------------------------------------
+// Storage formats of the population sets.  FP16 stores the shifted value
+// f - w_k * ref (ref = rho_ref for N, E_ref for g), rounded to nearest even.
+
+template <typename S, typename R> struct Store;
+
+template <> struct Store<double, double> {
+    __device__ static double load(const double* p, size_t i, double) { return p[i]; }
+    __device__ static void store(double* p, size_t i, double v, double) { p[i] = v; }
+};
+
+template <> struct Store<float, float> {
+    __device__ static float load(const float* p, size_t i, float) { return __ldg(p + i); }
+    __device__ static void store(float* p, size_t i, float v, float) { p[i] = v; }
+};
+
+template <> struct Store<__half, float> {
+    __device__ static float load(const __half* p, size_t i, float shift) {
+        return __half2float(__ldg(p + i)) + shift;
+    }
+    __device__ static void store(__half* p, size_t i, float v, float shift) {
+        p[i] = __float2half_rn(v - shift);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Parameters as seen by the kernels (arithmetic type R).
+
+template <typename R> struct KParams {
+    int nx, ny, nz;
+    long long nn;
+    R kappa, A, T0;
+    int barotropic;
+    R omega, omega_E;     // 1/tau, 1/tau_E
+    R c_v;
+    int chi_mode;
+    R lambda, chi;
+    R g[3];
+    int wall;
+    int T_fixed_lo, T_fixed_hi;
+    R T_lo, T_hi;
+    int pressure_work, conduction, pseudoforce;
+    R rho_ref, E_ref;     // FP16 shifts
+};
+
+// reduced van der Waals EOS scaled by kappa (Sec. 3); T0 when barotropic (Sec. 4)
+template <typename R>
+__device__ __forceinline__ R eos_pressure(const KParams<R>& p, R rho, R T) {
+    R Te = p.barotropic ? p.T0 : T;
+    return p.kappa * (R(8) * rho * Te / (R(3) - rho) - R(3) * rho * rho);
+}
+
+template <typename R>
+__device__ __forceinline__ R conductivity(const KParams<R>& p, R rho) {
+    return p.chi_mode ? rho * p.c_v * p.chi : p.lambda;
+}
+
+// ---------------------------------------------------------------------------
+// Neighbour index along the lattice with periodic x (and y for D3Q19) and a
+// periodic or walled last axis.  `ghost` is -1/+1 when the step crosses the
+// low/high wall; the index then points at the mirror node.
+
+struct Nb {
+    long long n;
+    int ghost;
+};
+
+template <int D>
+__device__ __forceinline__ Nb neighbour(int x, int y, int z, int dx, int dy, int dz, int nx, int ny,
+                                        int nz, int wall) {
+    Nb r;
+    r.ghost = 0;
+    int X = x + dx;
+    X = X < 0 ? X + nx : (X >= nx ? X - nx : X);
+    int Y, Z;
+    if (D == 2) {
+        Z = 0;
+        Y = y + dy;
+        if (wall) {
+            if (Y < 0) { Y = -1 - Y; r.ghost = -1; }
+            else if (Y >= ny) { Y = 2 * ny - 1 - Y; r.ghost = 1; }
+        } else {
+            Y = Y < 0 ? Y + ny : (Y >= ny ? Y - ny : Y);
+        }
+    } else {
+        Y = y + dy;
+        Y = Y < 0 ? Y + ny : (Y >= ny ? Y - ny : Y);
+        Z = z + dz;
+        if (wall) {
+            if (Z < 0) { Z = -1 - Z; r.ghost = -1; }
+            else if (Z >= nz) { Z = 2 * nz - 1 - Z; r.ghost = 1; }
+        } else {
+            Z = Z < 0 ? Z + nz : (Z >= nz ? Z - nz : Z);
+        }
+    }
+    r.n = ((long long)Z * ny + Y) * nx + X;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Equilibrium per unit density (Eq. (feq)) with theta = 1/3:
+//   e_k(u) = w_k (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u^2),  N_k^eq = rho e_k(u)
+// and its EDM increment (Eq. (edm)) per unit density:
+//   d_k = e_k(u + du) - e_k(u)
+//       = w_k (3 c.du + 9/2 c.du (2 c.u + c.du) - 3/2 du.(2u + du))
+// written as a difference so that FP32 keeps its precision for small du.
+
+template <int Q, typename R>
+__device__ __forceinline__ R cdot(int k, R ux, R uy, R uz) {
+    using V = Vel<Q>;
+    R s = R(0);
+    if (V::cx(k) == 1) s += ux; else if (V::cx(k) == -1) s -= ux;
+    if (V::cy(k) == 1) s += uy; else if (V::cy(k) == -1) s -= uy;
+    if (V::D == 3) { if (V::cz(k) == 1) s += uz; else if (V::cz(k) == -1) s -= uz; }
+    return s;
+}
+
+}  // namespace lbm

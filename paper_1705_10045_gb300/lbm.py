@@ -1,0 +1,276 @@
+"""Python binding of liblbm (include/lbm.h): argument marshalling only.
+
+Every step of the lattice update runs in the CUDA library; this module loads
+``_build/liblbm.so`` (built by ``paper_1705_10045_gb300.build``), mirrors the
+C structures with ctypes and passes host numpy arrays or device torch
+tensors by pointer.  There is no fallback: if the library is missing or no
+GPU is present, the calls raise.
+
+The functions carry the C names (``lbm_create``, ``lbm_init``, ...).  ``Lbm``
+is a small convenience wrapper around one handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+
+LBM_OK = 0
+LBM_ERR_INVALID_ARG = -1
+LBM_ERR_UNSTABLE_PARAMS = -2
+LBM_ERR_OOM = -3
+LBM_ERR_CUDA = -4
+LBM_ERR_NONPHYSICAL = -5
+
+LBM_D2Q9 = 9
+LBM_D3Q19 = 19
+LBM_STORE_FP64 = 0
+LBM_STORE_FP32 = 1
+LBM_STORE_FP16 = 2
+LBM_MEM_HOST = 0
+LBM_MEM_DEVICE = 1
+LBM_STEP_FUSED = 0
+LBM_STEP_THREE_LAUNCH = 1
+
+EXPORTED = ("lbm_default_params", "lbm_create", "lbm_init", "lbm_step", "lbm_moments", "lbm_diagnostics",
+            "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_sync", "lbm_launches_per_step",
+            "lbm_profile_step", "lbm_launch_name", "lbm_destroy", "lbm_last_error")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"liblbm error {code}: {msg}")
+        self.code = code
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("kappa", ctypes.c_double), ("A", ctypes.c_double), ("barotropic", ctypes.c_int), ("T0", ctypes.c_double),
+        ("tau", ctypes.c_double), ("tau_E", ctypes.c_double), ("c_v", ctypes.c_double),
+        ("chi_mode", ctypes.c_int), ("lambda_", ctypes.c_double), ("chi", ctypes.c_double),
+        ("gravity", ctypes.c_double * 3),
+        ("wall", ctypes.c_int), ("T_fixed_lo", ctypes.c_int), ("T_fixed_hi", ctypes.c_int),
+        ("T_lo", ctypes.c_double), ("T_hi", ctypes.c_double),
+        ("pressure_work", ctypes.c_int), ("conduction", ctypes.c_int), ("pseudoforce", ctypes.c_int),
+        ("storage", ctypes.c_int), ("rho_ref", ctypes.c_double), ("E_ref", ctypes.c_double),
+        ("step_kernel", ctypes.c_int),
+        ("stream", ctypes.c_void_p), ("device", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblbm.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1705_10045_gb300.build`")
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    P = ctypes.POINTER(lbm_params)
+    dp = ctypes.c_void_p   # host or device double*, passed as an address
+    lib.lbm_default_params.argtypes = [P]
+    lib.lbm_default_params.restype = None
+    lib.lbm_create.argtypes = [P, ctypes.POINTER(H)]
+    lib.lbm_init.argtypes = [H, dp, dp, dp, ctypes.c_int]
+    lib.lbm_step.argtypes = [H, ctypes.c_int]
+    lib.lbm_moments.argtypes = [H, dp, dp, dp, dp, ctypes.c_int]
+    lib.lbm_diagnostics.argtypes = [H, ctypes.POINTER(ctypes.c_double)]
+    lib.lbm_state_bytes.argtypes = [H]
+    lib.lbm_state_bytes.restype = ctypes.c_size_t
+    lib.lbm_get_state.argtypes = [H, ctypes.c_void_p, ctypes.c_int]
+    lib.lbm_set_state.argtypes = [H, ctypes.c_void_p, ctypes.c_int]
+    lib.lbm_sync.argtypes = [H]
+    lib.lbm_launches_per_step.argtypes = [H]
+    lib.lbm_profile_step.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    lib.lbm_profile_step.restype = ctypes.c_int
+    lib.lbm_launch_name.argtypes = [H, ctypes.c_int]
+    lib.lbm_launch_name.restype = ctypes.c_char_p
+    lib.lbm_destroy.argtypes = [H]
+    lib.lbm_destroy.restype = None
+    lib.lbm_last_error.argtypes = []
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    for name in ("lbm_create", "lbm_init", "lbm_step", "lbm_moments", "lbm_diagnostics", "lbm_get_state",
+                 "lbm_set_state", "lbm_sync", "lbm_launches_per_step"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != LBM_OK:
+        raise LbmError(rc, load().lbm_last_error().decode())
+    return rc
+
+
+def _addr(a):
+    """(address, mem flag) of a numpy array (host) or a torch tensor (host or device)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("host arrays must be C-contiguous float64")
+        return a.ctypes.data, LBM_MEM_HOST
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return a.data_ptr(), (LBM_MEM_DEVICE if a.is_cuda else LBM_MEM_HOST)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def lbm_default_params() -> lbm_params:
+    p = lbm_params()
+    load().lbm_default_params(ctypes.byref(p))
+    return p
+
+
+def make_params(**kw) -> lbm_params:
+    """Default parameters with keyword overrides (``lambda_`` for lambda)."""
+    p = lbm_default_params()
+    for k, v in kw.items():
+        if k == "lambda":
+            k = "lambda_"
+        if k == "gravity":
+            p.gravity = (ctypes.c_double * 3)(*[float(x) for x in v])
+        elif k == "stream":
+            p.stream = ctypes.c_void_p(int(v) if v is not None else 0)
+        else:
+            if not hasattr(p, k):
+                raise AttributeError(f"lbm_params has no field {k}")
+            setattr(p, k, int(v) if isinstance(v, bool) else v)
+    return p
+
+
+def lbm_create(params: lbm_params):
+    h = ctypes.c_void_p()
+    _check(load().lbm_create(ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def lbm_init(h, rho, u, eps):
+    (r, m1), (uu, m2), (e, m3) = _addr(rho), _addr(u), _addr(eps)
+    if not (m1 == m2 == m3):
+        raise ValueError("rho, u and eps must all live on the host or all on the device")
+    return _check(load().lbm_init(h, r, uu, e, m1))
+
+
+def lbm_step(h, n: int = 1):
+    return _check(load().lbm_step(h, int(n)))
+
+
+def lbm_moments(h, rho=None, u=None, T=None, P=None):
+    addrs = [_addr(a) for a in (rho, u, T, P)]
+    mems = {m for _, m in addrs if m is not None}
+    if len(mems) > 1:
+        raise ValueError("outputs must all live on the host or all on the device")
+    mem = mems.pop() if mems else LBM_MEM_HOST
+    return _check(load().lbm_moments(h, *[a for a, _ in addrs], mem))
+
+
+def lbm_diagnostics(h) -> np.ndarray:
+    out = (ctypes.c_double * 8)()
+    rc = load().lbm_diagnostics(h, out)
+    if rc not in (LBM_OK, LBM_ERR_NONPHYSICAL):
+        _check(rc)
+    return np.array(list(out))
+
+
+def lbm_state_bytes(h) -> int:
+    return int(load().lbm_state_bytes(h))
+
+
+def lbm_get_state(h, buf=None) -> np.ndarray:
+    if buf is None:
+        buf = np.empty(lbm_state_bytes(h), dtype=np.uint8)
+    _check(load().lbm_get_state(h, buf.ctypes.data, LBM_MEM_HOST))
+    return buf
+
+
+def lbm_set_state(h, buf: np.ndarray):
+    return _check(load().lbm_set_state(h, buf.ctypes.data, LBM_MEM_HOST))
+
+
+def lbm_sync(h):
+    return _check(load().lbm_sync(h))
+
+
+def lbm_launches_per_step(h) -> int:
+    return int(load().lbm_launches_per_step(h))
+
+
+def lbm_profile_step(h, n: int) -> dict:
+    """Run n steps with events around every launch; {kernel name: mean ms}."""
+    ms = (ctypes.c_double * 16)()
+    r = load().lbm_profile_step(h, int(n), ms, 16)
+    if r < 0:
+        _check(r)
+    return {load().lbm_launch_name(h, j).decode(): ms[j] for j in range(r)}
+
+
+def lbm_launch_name(h, j: int) -> str:
+    return load().lbm_launch_name(h, int(j)).decode()
+
+
+def lbm_destroy(h):
+    if h:
+        load().lbm_destroy(h)
+
+
+class Lbm:
+    """One simulation domain on the GPU (owns a liblbm handle)."""
+
+    def __init__(self, **kw):
+        self.params = make_params(**kw)
+        self.h = lbm_create(self.params)
+        self.Q = self.params.lattice
+        self.d = 2 if self.Q == LBM_D2Q9 else 3
+        self.shape = (self.params.nz, self.params.ny, self.params.nx)
+
+    def init(self, rho, u, eps):
+        return lbm_init(self.h, rho, u, eps)
+
+    def step(self, n: int = 1):
+        return lbm_step(self.h, n)
+
+    def moments(self) -> dict:
+        """Host copies of rho, u* (d planes), T and P."""
+        rho = np.empty(self.shape)
+        u = np.empty((self.d,) + self.shape)
+        T = np.empty(self.shape)
+        P = np.empty(self.shape)
+        lbm_moments(self.h, rho, u, T, P)
+        return {"rho": rho, "u": u, "T": T, "P": P}
+
+    def diagnostics(self) -> dict:
+        o = lbm_diagnostics(self.h)
+        return {"mass": o[0], "momentum": o[1:4], "energy": o[4], "clamps": int(o[5]), "bad": int(o[6]),
+                "steps": int(o[7])}
+
+    def get_state(self) -> np.ndarray:
+        return lbm_get_state(self.h)
+
+    def set_state(self, buf):
+        return lbm_set_state(self.h, buf)
+
+    def sync(self):
+        return lbm_sync(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

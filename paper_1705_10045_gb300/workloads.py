@@ -96,22 +96,25 @@ def flat_slab_2d(nx=128, ny=128, T=0.8, slab=64, width=4.0, noise=0.0, seed=1) -
 
 
 def moving_droplet_2d(n=512, T=0.85, radius=64.0, ux=0.05, uy=0.0, width=4.0, noise=1e-3, seed=2,
-                      hot_dT=0.05, hot_sigma=10.0, hot_offset=192.0) -> Fields:
-    """Circular drop in a periodic n x n box, whole fluid moving at (ux, uy), with
-    uniform density noise and a Gaussian hot spot in the vapour `hot_offset`
-    nodes from the drop centre along x (D2Q9 moving-droplet workload)."""
+                      hot_dT=0.05, hot_sigma=10.0, hot_offset=192.0, ny=None) -> Fields:
+    """Circular drop in a periodic n x n box (n x ny when ny is given), whole
+    fluid moving at (ux, uy), with uniform density noise and a Gaussian hot
+    spot in the vapour `hot_offset` nodes from the drop centre along x
+    (D2Q9 moving-droplet workload)."""
     rv, rl = coexistence(T)
-    y, x = np.meshgrid(np.arange(n, dtype=np.float64), np.arange(n, dtype=np.float64), indexing="ij")
-    cx = cy = n / 2.0
+    nx = n
+    ny = n if ny is None else ny
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    cx, cy = nx / 2.0, ny / 2.0
     s = radius - np.hypot(x - cx, y - cy)
     rho = _profile(s, rv, rl, width)[None]
     if noise:
         rho = rho + uniform_noise(rho.shape, noise, seed)
-    u = np.zeros((2, 1, n, n))
+    u = np.zeros((2, 1, ny, nx))
     u[0] = ux
     u[1] = uy
-    hx = (cx + hot_offset) % n
-    dx = np.minimum(np.abs(x - hx), n - np.abs(x - hx))
+    hx = (cx + hot_offset) % nx
+    dx = np.minimum(np.abs(x - hx), nx - np.abs(x - hx))
     Tf = T + hot_dT * np.exp(-(dx ** 2 + (y - cy) ** 2) / (2.0 * hot_sigma ** 2))
     return Fields(rho, u, Tf[None])
 

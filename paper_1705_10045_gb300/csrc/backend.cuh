@@ -33,14 +33,16 @@ template <typename R> KParams<R> make_kparams(const lbm_handle* h) {
 
 inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-// CTA tile of the fused kernel: 32 x 8 nodes of the xy plane for D3Q19, 64
-// nodes of a row for D2Q9.
-template <int Q> struct FusedTile;
-template <> struct FusedTile<9> { static constexpr int TX = 64, TY = 1; };
-template <> struct FusedTile<19> { static constexpr int TX = 32, TY = 8; };
+// CTA shape of the fused kernel: a TX x TY tile of consumer threads plus NP
+// producer threads.  D3Q19 uses 32 x 8 nodes with 160 producers (two CTAs per
+// SM) in FP32/FP16 and 256 producers in FP64; D2Q9 rows of 64.
+template <int Q, typename R> struct FusedTile;
+template <typename R> struct FusedTile<9, R> { static constexpr int TX = 64, TY = 1, NP = 64; };
+template <> struct FusedTile<19, float> { static constexpr int TX = 32, TY = 8, NP = 160; };
+template <> struct FusedTile<19, double> { static constexpr int TX = 32, TY = 8, NP = 256; };
 
 template <int Q, typename S, typename R> struct Impl {
-    static constexpr int TX = FusedTile<Q>::TX, TY = FusedTile<Q>::TY;
+    static constexpr int TX = FusedTile<Q, R>::TX, TY = FusedTile<Q, R>::TY, NP = FusedTile<Q, R>::NP;
 
     static int launches(const lbm_handle* h) { return h->p.step_kernel == LBM_STEP_THREE_LAUNCH ? 3 : 1; }
 
@@ -49,10 +51,10 @@ template <int Q, typename S, typename R> struct Impl {
         G.na = h->p.nx;
         G.nb = Q == 9 ? 1 : h->p.ny;
         G.nm = Q == 9 ? h->p.ny : h->p.nz;
-        // planes per CTA: enough CTAs for about four per SM on 152 SMs, and
-        // at least 8 planes so that the 4 extra ring planes stay a minority
+        // planes per CTA: enough CTAs for about two per SM on 152 SMs, and
+        // at least 8 planes so that the extra ring planes stay a minority
         const long long tiles = (long long)((G.na + TX - 1) / TX) * ((G.nb + TY - 1) / TY);
-        long long c = (G.nm * tiles + 607) / 608;
+        long long c = (G.nm * tiles + 303) / 304;
         c = c < 8 ? 8 : (c > 64 ? 64 : c);
         G.chunk = (int)(c > G.nm ? G.nm : c);
         return G;
@@ -61,13 +63,13 @@ template <int Q, typename S, typename R> struct Impl {
     static void launch_fused(lbm_handle* h, const KParams<R>& kp) {
         const MarchGeom G = geometry(h);
         const size_t smem = FusedShape<TX, TY>::template smem_bytes<R>();
-        auto kern = fused_step_kernel<Q, S, R, TX, TY>;
+        auto kern = fused_step_kernel<Q, S, R, TX, TY, NP>;
         if (!h->fused_ready) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             h->fused_ready = true;
         }
         const dim3 grid((G.na + TX - 1) / TX, (G.nb + TY - 1) / TY, (G.nm + G.chunk - 1) / G.chunk);
-        kern<<<grid, TX * TY, smem, h->stream>>>((const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], kp, G,
+        kern<<<grid, TX * TY + NP, smem, h->stream>>>((const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], kp, G,
                                                  (Counters*)h->cnt);
         h->cur ^= 1;
     }

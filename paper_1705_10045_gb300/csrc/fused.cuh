@@ -6,21 +6,29 @@
 // force there, and the force needs Phi one node further out, so one step of a
 // node depends on the moments of a 2-ring around it.  A CTA owns a TX x TY
 // tile of the plane normal to the last lattice axis (z for D3Q19, y for D2Q9)
-// and marches along that axis through a chunk of planes.  Per plane m it
-//   M: loads the populations of the (TX+4) x (TY+4) ring region of plane m and
-//      keeps rho, u, T, Phi in a 5-plane shared-memory ring buffer;
-//   F: computes du = F/rho (Sec. 3 force + gravity) on the (TX+2) x (TY+2)
-//      region of plane m-1 into a 3-plane buffer;
-//   C: for the TX x TY nodes of plane m-2 forms dE by finite differences,
-//      reloads the node's populations (an L2 hit: plane m-2 was read two
-//      iterations earlier), collides N and g and pushes them to x + c_k.
-// Ring nodes are recomputed by neighbouring CTAs from L2 rather than
-// exchanged.  D2Q9 runs the same code as a lattice with one y node: its
-// lattice y axis is the march axis and its tile is TX x 1.
+// and marches along that axis through a chunk of planes.  Three stages work
+// on a plane each:
+//   M: loads the populations of the (TX+4) x (TY+4) ring region of a plane,
+//      keeps Phi on that region and rho, u, T on the (TX+2) x (TY+2) 1-ring
+//      region in shared-memory plane buffers;
+//   F: computes du = F/rho (Sec. 3 force + gravity) on the 1-ring region;
+//   C: for the TX x TY nodes of a plane forms dE by finite differences,
+//      reloads the node's populations (an L2 hit: the M stage read them a few
+//      planes earlier), collides N and g and pushes them to x + c_k.
+// The CTA is warp-specialised: producer warps run M on plane i and F on
+// plane i-1 while consumer warps (one thread per tile node) run C on plane
+// i-3, so population loads overlap the collision arithmetic.  One CTA-wide
+// barrier per plane hands the buffers over; a named barrier orders M before
+// F inside the producer warps.  Ring nodes are recomputed by neighbouring
+// CTAs from L2 rather than exchanged.  D2Q9 runs the same code as a lattice
+// with one y node: its lattice y axis is the march axis and its tile is
+// TX x 1.
 //
 // Index arithmetic is kept out of the inner loops: the wrapped ring
-// coordinates of a CTA are tabulated once in shared memory, and each thread
-// precomputes the +-1 node offsets of its own node along every axis.
+// coordinates of a CTA are tabulated once in shared memory, and each
+// consumer thread precomputes the +-1 node offsets of its node along every
+// axis.  The force stencil and the collision work on opposite-direction pairs
+// (c_{k+1} = -c_k), which share the even part of every term.
 #pragma once
 
 #include "kernels.cuh"
@@ -47,18 +55,22 @@ struct MarchGeom {
     int chunk;   // planes per CTA along the march axis
 };
 
+// Plane buffers: Phi for 3 planes, rho/u/T for 5 planes, du for 4 planes
+// (the consumer trails the producer by three planes).
 template <int TX, int TY> struct FusedShape {
     static constexpr int RB = TY > 1 ? 2 : 0;           // ring width across b (none for D2Q9)
-    static constexpr int RW = TX + 4;                   // ring region width (a)
-    static constexpr int RH = TY + 2 * RB;              // ring region height (b)
+    static constexpr int RW = TX + 4;                   // 2-ring region (Phi)
+    static constexpr int RH = TY + 2 * RB;
     static constexpr int R = RW * RH;
-    static constexpr int FW = TX + 2;                   // force region
-    static constexpr int FB = RB / 2;
+    static constexpr int FB = RB / 2;                   // 1-ring region (rho, u, T, du)
+    static constexpr int FW = TX + 2;
     static constexpr int FH = TY + 2 * FB;
     static constexpr int F = FW * FH;
-    static constexpr int kFields = 6;                   // Phi, rho, ua, ub, um, T
+    static constexpr int kRut = 5;                      // rho, ua, ub, um, T
+    static constexpr int kPhiSlots = 3, kRutSlots = 5, kDuSlots = 4;
     template <typename R_> static constexpr size_t smem_bytes() {
-        return sizeof(R_) * ((size_t)5 * kFields * R + (size_t)3 * 3 * F) + sizeof(int) * (RW + RH);
+        return sizeof(R_) * ((size_t)kPhiSlots * R + (size_t)kRutSlots * kRut * F + (size_t)kDuSlots * 3 * F) +
+               sizeof(int) * (RW + RH);
     }
 };
 
@@ -67,234 +79,283 @@ __device__ __forceinline__ int wrapi(int i, int n) {
     return i < 0 ? i + n : i;
 }
 
-template <int Q, typename S, typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst,
-                                                            KParams<R> p, MarchGeom G, Counters* cnt) {
+__device__ __forceinline__ int slotn(int m, int n) { return ((m % n) + n) % n; }
+
+template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
     using V = Vel<Q>;
     using M = MVel<Q>;
     using Sh = FusedShape<TX, TY>;
-    constexpr int NT = TX * TY;
-    constexpr int RB = Sh::RB, RW = Sh::RW, RH = Sh::RH, R_ = Sh::R, FW = Sh::FW, FB = Sh::FB, F_ = Sh::F;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* fs = reinterpret_cast<R*>(smem_raw);               // [5][kFields][R_]
-    R* dus = fs + 5 * Sh::kFields * R_;                    // [3][3][F_]
-    int* ring_a = reinterpret_cast<int*>(dus + 3 * 3 * F_);   // wrapped a of ring column
-    int* ring_b = ring_a + RW;                                // wrapped b * na of ring row
+    static constexpr int RB = Sh::RB, RW = Sh::RW, RH = Sh::RH, R_ = Sh::R, FW = Sh::FW, FB = Sh::FB, F_ = Sh::F;
 
-    const size_t nn = (size_t)p.nn;
-    const int na = G.na, nb = G.nb, nm = G.nm;
-    const int plane_n = na * nb;
-    const int tid = threadIdx.x;
-    const int a0 = blockIdx.x * TX, b0 = blockIdx.y * TY;
-    const int zb = blockIdx.z * G.chunk;
-    const int ze = min(zb + G.chunk, nm);
-    const bool walls = p.wall;
-    const R third = R(1.0 / 3.0);
+    R* phis;     // [kPhiSlots][R_]
+    R* ruts;     // [kRutSlots][kRut][F_]
+    R* dus;      // [kDuSlots][3][F_]
+    int* ring_a; // wrapped a of ring column
+    int* ring_b; // wrapped b * na of ring row
+    const S* __restrict__ src;
+    S* __restrict__ dst;
+    const KParams<R>* p;
+    MarchGeom G;
+    size_t nn;
+    int plane_n;
 
-    for (int i = tid; i < RW; i += NT) ring_a[i] = wrapi(a0 + i - 2, na);
-    for (int i = tid; i < RH; i += NT) ring_b[i] = wrapi(b0 + i - RB, nb) * na;
-
-    auto fld = [&](int slot, int f, int r) -> R& { return fs[((slot * Sh::kFields) + f) * R_ + r]; };
-    auto du = [&](int slot, int c, int r) -> R& { return dus[(slot * 3 + c) * F_ + r]; };
+    __device__ R& phi(int slot, int r) const { return phis[slot * R_ + r]; }
+    __device__ R& rut(int slot, int f, int r) const { return ruts[(slot * Sh::kRut + f) * F_ + r]; }
+    __device__ R& du(int slot, int c, int r) const { return dus[(slot * 3 + c) * F_ + r]; }
     // Buffer slots are keyed by the unwrapped plane index the M stage loaded
     // (a periodic plane -1 holds the data of plane nm-1); across a wall a
     // stencil read goes to the mirror plane instead.
-    auto mplane = [&](int m) -> int {
-        if (!walls) return m;
-        return m < 0 ? -1 - m : (m >= nm ? 2 * nm - 1 - m : m);
-    };
-    auto slot5 = [](int m) { return ((m % 5) + 5) % 5; };
-    auto slot3 = [](int m) { return ((m % 3) + 3) % 3; };
+    __device__ int mplane(int m) const {
+        if (!p->wall) return m;
+        return m < 0 ? -1 - m : (m >= G.nm ? 2 * G.nm - 1 - m : m);
+    }
 
-    // this thread's node in the tile and its +-1 offsets along a and b
+    // M: moments of plane m on the ring region, ring nodes t, t + nt, ...
+    __device__ void m_stage(int m, int t, int nt) const {
+        const int plane_off = wrapi(m, G.nm) * plane_n;
+        const int sp = slotn(m, Sh::kPhiSlots), sr = slotn(m, Sh::kRutSlots);
+        const R third = R(1.0 / 3.0);
+        for (int r = t; r < R_; r += nt) {
+            const int ra = r % RW, rb = r / RW;
+            const size_t n = (size_t)(plane_off + ring_b[rb] + ring_a[ra]);
+            R fN[Q], fG[Q];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                fN[k] = Store<S, R>::load(src, (size_t)k * nn + n, R(V::w(k)) * p->rho_ref);
+                fG[k] = Store<S, R>::load(src, (size_t)(Q + k) * nn + n, R(V::w(k)) * p->E_ref);
+            }
+            R rho = 0, ja = 0, jb = 0, jm = 0, E = 0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const R f = fN[k];
+                rho += f;
+                if (M::a(k) == 1) ja += f; else if (M::a(k) == -1) ja -= f;
+                if (M::b(k) == 1) jb += f; else if (M::b(k) == -1) jb -= f;
+                if (M::m(k) == 1) jm += f; else if (M::m(k) == -1) jm -= f;
+            }
+#pragma unroll
+            for (int k = 0; k < Q; ++k) E += fG[k];
+            const R T = E / (rho * p->c_v);
+            const R U = eos_pressure(*p, rho, T) - rho * third;
+            phi(sp, r) = U < R(0) ? sqrt(-U) : R(0);
+            const int fa = ra - 1, fb = rb - (RB - FB);
+            if (fa >= 0 && fa < FW && fb >= 0 && fb < Sh::FH) {
+                const int f = fb * FW + fa;
+                const R inv_rho = R(1) / rho;
+                rut(sr, 0, f) = rho;
+                rut(sr, 1, f) = ja * inv_rho;
+                rut(sr, 2, f) = jb * inv_rho;
+                rut(sr, 3, f) = jm * inv_rho;
+                rut(sr, 4, f) = T;
+            }
+        }
+    }
+
+    // F: du = F/rho on the 1-ring region of plane f, region nodes t, t + nt, ...
+    __device__ void f_stage(int f, int t, int nt) const {
+        const int sp0 = slotn(f, Sh::kPhiSlots), spm = slotn(mplane(f - 1), Sh::kPhiSlots),
+                  spp = slotn(mplane(f + 1), Sh::kPhiSlots);
+        const int sr = slotn(f, Sh::kRutSlots), sd = slotn(f, Sh::kDuSlots);
+        const R A = p->A, B = R(1) - R(2) * p->A, inv_alpha = R(1.0 / V::alpha);
+        const R gv[3] = {p->g[0], Q == 9 ? R(0) : p->g[1], Q == 9 ? p->g[1] : p->g[2]};
+        const R G2 = R(V::G(Q - 1));   // next-nearest weight (1/4 or 1/2)
+        for (int r = t; r < F_; r += nt) {
+            const int ra = r % FW + 1, rb = r / FW + (RB - FB);
+            // opposite directions pair up: G Phi(x+e) e + G Phi(x-e)(-e) = G (Phi+ - Phi-) e,
+            // and the Phi^2 term is G (Phi+ - Phi-)(Phi+ + Phi-) e
+            R n1[3] = {0, 0, 0}, n2[3] = {0, 0, 0}, q1[3] = {0, 0, 0}, q2[3] = {0, 0, 0};
+#pragma unroll
+            for (int k = 1; k < Q; k += 2) {
+                const int s_p = M::m(k) == 0 ? sp0 : (M::m(k) > 0 ? spp : spm);
+                const int s_m = M::m(k) == 0 ? sp0 : (M::m(k) > 0 ? spm : spp);
+                const R pp = phi(s_p, (rb + M::b(k)) * RW + ra + M::a(k));
+                const R pm = phi(s_m, (rb - M::b(k)) * RW + ra - M::a(k));
+                const R d = pp - pm;
+                const R d2 = d * (pp + pm);
+                const bool nearest = M::a(k) * M::a(k) + M::b(k) * M::b(k) + M::m(k) * M::m(k) == 1;
+                R* s1 = nearest ? n1 : q1;
+                R* s2 = nearest ? n2 : q2;
+                if (M::a(k) == 1) { s1[0] += d2; s2[0] += d; } else if (M::a(k) == -1) { s1[0] -= d2; s2[0] -= d; }
+                if (M::b(k) == 1) { s1[1] += d2; s2[1] += d; } else if (M::b(k) == -1) { s1[1] -= d2; s2[1] -= d; }
+                if (M::m(k) == 1) { s1[2] += d2; s2[2] += d; } else if (M::m(k) == -1) { s1[2] -= d2; s2[2] -= d; }
+            }
+            const R rho = rut(sr, 0, r), ph0 = phi(sp0, rb * RW + ra);
+            const R scale = inv_alpha / rho;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const R s1 = n1[a] + G2 * q1[a], s2 = n2[a] + G2 * q2[a];
+                du(sd, a, r) = (A * s1 + B * ph0 * s2) * scale + gv[a];
+            }
+        }
+    }
+
+    // C: energy change, collision and push of the node (ta, tb) of plane c
+    __device__ void c_stage(int c, int ta, int tb, int n_ab, int dA_m, int dA_p, int dB_m, int dB_p,
+                            Counters* cnt) const {
+        const bool walls = p->wall;
+        const int nm = G.nm;
+        const R third = R(1.0 / 3.0);
+        const int sr = slotn(c, Sh::kRutSlots), sd = slotn(c, Sh::kDuSlots);
+        const int fc = (tb + FB) * FW + ta + 1;        // 1-ring index of the node
+        const R rho = rut(sr, 0, fc), T = rut(sr, 4, fc);
+        const R u[3] = {rut(sr, 1, fc), rut(sr, 2, fc), rut(sr, 3, fc)};
+        const R dv[3] = {du(sd, 0, fc), du(sd, 1, fc), du(sd, 2, fc)};
+
+        // finite-difference dE along a, b and the march axis (Sec. 4, Sec. 6.2)
+        R div = 0, cond = 0;
+        const R lc = conductivity(*p, rho);
+        auto axis = [&](R uu, R ud, R Tu, R Td, R ru, R rd) {
+            div += (uu - ud) / R(2);
+            const R lu = (lc + conductivity(*p, ru)) / R(2);
+            const R ld = (lc + conductivity(*p, rd)) / R(2);
+            cond += lu * (Tu - T) - ld * (T - Td);
+        };
+        axis(rut(sr, 1, fc + 1) + du(sd, 0, fc + 1) / R(2), rut(sr, 1, fc - 1) + du(sd, 0, fc - 1) / R(2),
+             rut(sr, 4, fc + 1), rut(sr, 4, fc - 1), rut(sr, 0, fc + 1), rut(sr, 0, fc - 1));
+        if (Q == 19)
+            axis(rut(sr, 2, fc + FW) + du(sd, 1, fc + FW) / R(2), rut(sr, 2, fc - FW) + du(sd, 1, fc - FW) / R(2),
+                 rut(sr, 4, fc + FW), rut(sr, 4, fc - FW), rut(sr, 0, fc + FW), rut(sr, 0, fc - FW));
+        {   // march axis: neighbouring planes, or the node itself mirrored across a wall
+            const bool gu = walls && c + 1 >= nm, gd = walls && c - 1 < 0;
+            const int su = slotn(c + 1, Sh::kRutSlots), sdn = slotn(c - 1, Sh::kRutSlots);
+            const int du_u = slotn(c + 1, Sh::kDuSlots), du_d = slotn(c - 1, Sh::kDuSlots);
+            const R own = -(u[2] + dv[2] / R(2));
+            const R uu = gu ? own : rut(su, 3, fc) + du(du_u, 2, fc) / R(2);
+            const R ud = gd ? own : rut(sdn, 3, fc) + du(du_d, 2, fc) / R(2);
+            const R Tu = gu ? (p->T_fixed_hi ? R(2) * p->T_hi - T : T) : rut(su, 4, fc);
+            const R Td = gd ? (p->T_fixed_lo ? R(2) * p->T_lo - T : T) : rut(sdn, 4, fc);
+            const R ru = gu ? rho : rut(su, 0, fc);
+            const R rd = gd ? rho : rut(sdn, 0, fc);
+            axis(uu, ud, Tu, Td, ru, rd);
+        }
+        const R P = eos_pressure(*p, rho, T);
+        R dE = 0;
+        if (p->pressure_work) dE += -P * div;
+        if (p->conduction) dE += cond;
+        if (P - rho * third >= R(0)) atomicAdd(&cnt->clamps, 1ull);
+
+        const int n = c * plane_n + n_ab;
+        R hv[Q];
+        R E = 0;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            hv[k] = Store<S, R>::load(src, (size_t)(Q + k) * nn + n, R(V::w(k)) * p->E_ref);
+            E += hv[k];
+        }
+        if (!(finite_pos(rho) && finite_pos(E))) atomicAdd(&cnt->bad, 1ull);
+        const R dEoverE = dE / E;
+
+        // node offsets of x + c_k: +-1 along a and b (periodic), along the
+        // march axis periodic or bounced at a wall
+        const int dM_m = (c == 0 ? nm - 1 : -1) * plane_n, dM_p = (c == nm - 1 ? 1 - nm : 1) * plane_n;
+        const bool wall_lo = walls && c == 0, wall_hi = walls && c == nm - 1;
+
+        // Collision, Eq. (lbe)/(edm)/(gk), written per node as
+        //   N*_k = (1 - omega) N_k + rho (omega e0_k + de_k)
+        //   g*_k = (1 - omega_E + dE/E) g_k + E (omega_E e0_k + [pseudoforce] de_k)
+        // with e0 = N^eq(rho,u)/rho and de = (N^eq(rho,u+du) - N^eq(rho,u))/rho.
+        // For opposite directions k, k+1 (c -> -c) both split into an even
+        // part (shared) and an odd part (sign flip).
+        const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const R dsq = dv[0] * (R(2) * u[0] + dv[0]) + dv[1] * (R(2) * u[1] + dv[1]) +
+                      dv[2] * (R(2) * u[2] + dv[2]);
+        const R base0 = R(1) - R(1.5) * usq, dbase = R(-1.5) * dsq;
+        const R om = p->omega, omE = p->omega_E;
+        const R fN = R(1) - om, fG = R(1) - omE + dEoverE;
+        const R pf = p->pseudoforce ? R(1) : R(0);
+
+        auto emit = [&](int k, R e0, R de, R fv, R hvk) {
+            const R fo = fv * fN + rho * (om * e0 + de);
+            const R ho = hvk * fG + E * (omE * e0 + pf * de);
+            // push to x + c_k, or bounce back at a wall on the march axis
+            const bool bounce = (M::m(k) == -1 && wall_lo) || (M::m(k) == 1 && wall_hi);
+            const int ko = bounce ? opposite(k) : k;
+            int to = n;
+            if (!bounce) {
+                if (M::a(k) == 1) to += dA_p; else if (M::a(k) == -1) to += dA_m;
+                if (M::b(k) == 1) to += dB_p; else if (M::b(k) == -1) to += dB_m;
+                if (M::m(k) == 1) to += dM_p; else if (M::m(k) == -1) to += dM_m;
+            }
+            // opposite directions share a weight, so the FP16 shift of slot ko is w_k ref
+            const R wk = R(V::w(k));
+            Store<S, R>::store(dst, (size_t)ko * nn + to, fo, wk * p->rho_ref);
+            Store<S, R>::store(dst, (size_t)(Q + ko) * nn + to, ho, wk * p->E_ref);
+        };
+        {
+            const R w0 = R(V::w(0));
+            emit(0, w0 * base0, w0 * dbase, Store<S, R>::load(src, n, w0 * p->rho_ref), hv[0]);
+        }
+#pragma unroll
+        for (int k = 1; k < Q; k += 2) {
+            const R wk = R(V::w(k));
+            R cu = 0, cd = 0;
+            if (M::a(k) == 1) { cu += u[0]; cd += dv[0]; } else if (M::a(k) == -1) { cu -= u[0]; cd -= dv[0]; }
+            if (M::b(k) == 1) { cu += u[1]; cd += dv[1]; } else if (M::b(k) == -1) { cu -= u[1]; cd -= dv[1]; }
+            if (M::m(k) == 1) { cu += u[2]; cd += dv[2]; } else if (M::m(k) == -1) { cu -= u[2]; cd -= dv[2]; }
+            const R ev = wk * (base0 + R(4.5) * cu * cu), od = wk * (R(3) * cu);
+            const R dv_e = wk * (R(4.5) * cd * (R(2) * cu + cd) + dbase), dv_o = wk * (R(3) * cd);
+            const R fa = Store<S, R>::load(src, (size_t)k * nn + n, wk * p->rho_ref);
+            const R fb = Store<S, R>::load(src, (size_t)(k + 1) * nn + n, wk * p->rho_ref);
+            emit(k, ev + od, dv_e + dv_o, fa, hv[k]);
+            emit(k + 1, ev - od, dv_e - dv_o, fb, hv[k + 1]);
+        }
+    }
+};
+
+// Producer/consumer fused step.  Threads [0, TX*TY) are consumers (one per
+// tile node), threads [TX*TY, TX*TY + NP) producers.
+template <int Q, typename S, typename R, int TX, int TY, int NP>
+__global__ void __launch_bounds__(TX* TY + NP) fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                                                                 KParams<R> p, MarchGeom G, Counters* cnt) {
+    using St = FusedStages<Q, S, R, TX, TY>;
+    using Sh = typename St::Sh;
+    constexpr int NC = TX * TY, NT = NC + NP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    St st;
+    st.phis = reinterpret_cast<R*>(smem_raw);
+    st.ruts = st.phis + Sh::kPhiSlots * Sh::R;
+    st.dus = st.ruts + Sh::kRutSlots * Sh::kRut * Sh::F;
+    st.ring_a = reinterpret_cast<int*>(st.dus + Sh::kDuSlots * 3 * Sh::F);
+    st.ring_b = st.ring_a + Sh::RW;
+    st.src = src;
+    st.dst = dst;
+    st.p = &p;
+    st.G = G;
+    st.nn = (size_t)p.nn;
+    st.plane_n = G.na * G.nb;
+
+    const int tid = threadIdx.x;
+    const int a0 = blockIdx.x * TX, b0 = blockIdx.y * TY;
+    const int zb = blockIdx.z * G.chunk;
+    const int ze = min(zb + G.chunk, G.nm);
+    const bool walls = p.wall;
+    for (int i = tid; i < Sh::RW; i += NT) st.ring_a[i] = wrapi(a0 + i - 2, G.na);
+    for (int i = tid; i < Sh::RH; i += NT) st.ring_b[i] = wrapi(b0 + i - Sh::RB, G.nb) * G.na;
+
+    const bool producer = tid >= NC;
+    // consumer node and its +-1 offsets along a and b
     const int ta = tid % TX, tb = tid / TX;
     const int ga = a0 + ta, gb = b0 + tb;
-    const bool owns = ga < na && gb < nb;
-    const int base_ab = gb * na + ga;
-    const int dA_m = ga == 0 ? na - 1 : -1, dA_p = ga == na - 1 ? 1 - na : 1;
-    const int dB_m = (gb == 0 ? nb - 1 : -1) * na, dB_p = (gb == nb - 1 ? 1 - nb : 1) * na;
-
+    const bool owns = !producer && ga < G.na && gb < G.nb;
+    const int n_ab = gb * G.na + ga;
+    const int dA_m = ga == 0 ? G.na - 1 : -1, dA_p = ga == G.na - 1 ? 1 - G.na : 1;
+    const int dB_m = (gb == 0 ? G.nb - 1 : -1) * G.na, dB_p = (gb == G.nb - 1 ? 1 - G.nb : 1) * G.na;
     __syncthreads();
 
-    for (int m = zb - 2; m < ze + 2; ++m) {
-        // ---- M: moments of plane m on the ring region -------------------
-        const bool m_real = walls ? (m >= 0 && m < nm) : true;
-        if (m_real) {
-            const int plane_off = wrapi(m, nm) * plane_n;
-            const int sl = slot5(m);
-            for (int r = tid; r < R_; r += NT) {
-                const int ra = r % RW, rb = r / RW;
-                const size_t n = (size_t)(plane_off + ring_b[rb] + ring_a[ra]);
-                R fN[Q], fG[Q];
-#pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    fN[k] = Store<S, R>::load(src, (size_t)k * nn + n, R(V::w(k)) * p.rho_ref);
-                    fG[k] = Store<S, R>::load(src, (size_t)(Q + k) * nn + n, R(V::w(k)) * p.E_ref);
-                }
-                R rho = 0, ja = 0, jb = 0, jm = 0, E = 0;
-#pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    const R f = fN[k];
-                    rho += f;
-                    if (M::a(k) == 1) ja += f; else if (M::a(k) == -1) ja -= f;
-                    if (M::b(k) == 1) jb += f; else if (M::b(k) == -1) jb -= f;
-                    if (M::m(k) == 1) jm += f; else if (M::m(k) == -1) jm -= f;
-                }
-#pragma unroll
-                for (int k = 0; k < Q; ++k) E += fG[k];
-                const R T = E / (rho * p.c_v);
-                const R U = eos_pressure(p, rho, T) - rho * third;
-                fld(sl, 0, r) = U < R(0) ? sqrt(-U) : R(0);
-                fld(sl, 1, r) = rho;
-                fld(sl, 2, r) = ja / rho;
-                fld(sl, 3, r) = jb / rho;
-                fld(sl, 4, r) = jm / rho;
-                fld(sl, 5, r) = T;
-            }
+    for (int i = zb - 2; i < ze + 3; ++i) {
+        if (producer) {
+            const int t = tid - NC;
+            const bool m_need = i <= ze + 1 && (walls ? (i >= 0 && i < G.nm) : true);
+            if (m_need) st.m_stage(i, t, NP);
+            asm volatile("bar.sync 1, %0;" ::"r"(NP));
+            const int f = i - 1;
+            const bool f_need = f >= zb - 1 && f <= ze && (walls ? (f >= 0 && f < G.nm) : true);
+            if (f_need) st.f_stage(f, t, NP);
+        } else {
+            const int c = i - 3;
+            if (c >= zb && c < ze && owns) st.c_stage(c, ta, tb, n_ab, dA_m, dA_p, dB_m, dB_p, cnt);
         }
         __syncthreads();
-
-        // ---- F: du = F/rho on the force region of plane f = m - 1 --------
-        const int f = m - 1;
-        const bool f_need = f >= zb - 1 && f <= ze && (walls ? (f >= 0 && f < nm) : true);
-        if (f_need) {
-            const int sl = slot5(f), sd = slot3(f);
-            const int slm = slot5(mplane(f - 1)), slp = slot5(mplane(f + 1));
-            const R A = p.A, B = R(1) - R(2) * p.A, inv_alpha = R(1.0 / V::alpha);
-            const R g_a = p.g[0], g_b = Q == 9 ? R(0) : p.g[1], g_m = Q == 9 ? p.g[1] : p.g[2];
-            for (int r = tid; r < F_; r += NT) {
-                const int fa = r % FW, fb = r / FW;
-                const int ra = fa + 1, rb = fb + (RB - FB);
-                R s1a = 0, s1b = 0, s1m = 0, s2a = 0, s2b = 0, s2m = 0;
-#pragma unroll
-                for (int k = 1; k < Q; ++k) {
-                    const int s = M::m(k) == 0 ? sl : (M::m(k) > 0 ? slp : slm);
-                    const R ph = fld(s, 0, (rb + M::b(k)) * RW + ra + M::a(k));
-                    const R t1 = R(V::G(k)) * ph * ph;
-                    const R t2 = R(V::G(k)) * ph;
-                    if (M::a(k) == 1) { s1a += t1; s2a += t2; } else if (M::a(k) == -1) { s1a -= t1; s2a -= t2; }
-                    if (M::b(k) == 1) { s1b += t1; s2b += t2; } else if (M::b(k) == -1) { s1b -= t1; s2b -= t2; }
-                    if (M::m(k) == 1) { s1m += t1; s2m += t2; } else if (M::m(k) == -1) { s1m -= t1; s2m -= t2; }
-                }
-                const int rc = rb * RW + ra;
-                const R rho = fld(sl, 1, rc), ph0 = fld(sl, 0, rc);
-                du(sd, 0, r) = ((A * s1a + B * ph0 * s2a) * inv_alpha + rho * g_a) / rho;
-                du(sd, 1, r) = ((A * s1b + B * ph0 * s2b) * inv_alpha + rho * g_b) / rho;
-                du(sd, 2, r) = ((A * s1m + B * ph0 * s2m) * inv_alpha + rho * g_m) / rho;
-            }
-        }
-        __syncthreads();
-
-        // ---- C: energy change, collision and push of plane c = m - 2 -----
-        const int c = m - 2;
-        if (c >= zb && c < ze && owns) {
-            const int sl = slot5(c), sd = slot3(c);
-            const int rc = (tb + RB) * RW + ta + 2;        // ring index of the node
-            const int fc = (tb + FB) * FW + ta + 1;        // force-region index
-            const R rho = fld(sl, 1, rc), T = fld(sl, 5, rc);
-            const R u[3] = {fld(sl, 2, rc), fld(sl, 3, rc), fld(sl, 4, rc)};
-            const R dv[3] = {du(sd, 0, fc), du(sd, 1, fc), du(sd, 2, fc)};
-
-            // finite-difference dE along a, b and the march axis
-            R div = 0, cond = 0;
-            const R lc = conductivity(p, rho);
-            {   // a: same plane, ring neighbours
-                const R uu = fld(sl, 2, rc + 1) + du(sd, 0, fc + 1) / R(2);
-                const R ud = fld(sl, 2, rc - 1) + du(sd, 0, fc - 1) / R(2);
-                div += (uu - ud) / R(2);
-                const R Tu = fld(sl, 5, rc + 1), Td = fld(sl, 5, rc - 1);
-                const R lu = (lc + conductivity(p, fld(sl, 1, rc + 1))) / R(2);
-                const R ld = (lc + conductivity(p, fld(sl, 1, rc - 1))) / R(2);
-                cond += lu * (Tu - T) - ld * (T - Td);
-            }
-            if (Q == 19) {   // b: same plane
-                const R uu = fld(sl, 3, rc + RW) + du(sd, 1, fc + FW) / R(2);
-                const R ud = fld(sl, 3, rc - RW) + du(sd, 1, fc - FW) / R(2);
-                div += (uu - ud) / R(2);
-                const R Tu = fld(sl, 5, rc + RW), Td = fld(sl, 5, rc - RW);
-                const R lu = (lc + conductivity(p, fld(sl, 1, rc + RW))) / R(2);
-                const R ld = (lc + conductivity(p, fld(sl, 1, rc - RW))) / R(2);
-                cond += lu * (Tu - T) - ld * (T - Td);
-            }
-            {   // march axis: neighbouring planes, or the node itself mirrored across a wall
-                const bool gu = walls && c + 1 >= nm, gd = walls && c - 1 < 0;
-                const int su = slot5(c + 1), sdn = slot5(c - 1), du_u = slot3(c + 1), du_d = slot3(c - 1);
-                R uu, ud, Tu, Td, ru, rd;
-                if (gu) {
-                    uu = -(u[2] + dv[2] / R(2));
-                    Tu = p.T_fixed_hi ? R(2) * p.T_hi - T : T;
-                    ru = rho;
-                } else {
-                    uu = fld(su, 4, rc) + du(du_u, 2, fc) / R(2);
-                    Tu = fld(su, 5, rc);
-                    ru = fld(su, 1, rc);
-                }
-                if (gd) {
-                    ud = -(u[2] + dv[2] / R(2));
-                    Td = p.T_fixed_lo ? R(2) * p.T_lo - T : T;
-                    rd = rho;
-                } else {
-                    ud = fld(sdn, 4, rc) + du(du_d, 2, fc) / R(2);
-                    Td = fld(sdn, 5, rc);
-                    rd = fld(sdn, 1, rc);
-                }
-                div += (uu - ud) / R(2);
-                const R lu = (lc + conductivity(p, ru)) / R(2);
-                const R ld = (lc + conductivity(p, rd)) / R(2);
-                cond += lu * (Tu - T) - ld * (T - Td);
-            }
-            const R P = eos_pressure(p, rho, T);
-            R dE = 0;
-            if (p.pressure_work) dE += -P * div;
-            if (p.conduction) dE += cond;
-            if (P - rho * third >= R(0)) atomicAdd(&cnt->clamps, 1ull);
-
-            const int n = c * plane_n + base_ab;
-            R hv[Q];
-            R E = 0;
-#pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                hv[k] = Store<S, R>::load(src, (size_t)(Q + k) * nn + n, R(V::w(k)) * p.E_ref);
-                E += hv[k];
-            }
-            if (!(finite_pos(rho) && finite_pos(E))) atomicAdd(&cnt->bad, 1ull);
-            const R dEoverE = dE / E;
-
-            // node offsets of x + c_k: +-1 along a and b (periodic), along the
-            // march axis periodic or bounced at a wall
-            const int dM_m = (c == 0 ? nm - 1 : -1) * plane_n, dM_p = (c == nm - 1 ? 1 - nm : 1) * plane_n;
-            const bool wall_lo = walls && c == 0, wall_hi = walls && c == nm - 1;
-
-            const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            const R dsq = dv[0] * (R(2) * u[0] + dv[0]) + dv[1] * (R(2) * u[1] + dv[1]) +
-                          dv[2] * (R(2) * u[2] + dv[2]);
-#pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const R wk = R(V::w(k));
-                R cu = 0, cd = 0;
-                if (M::a(k) == 1) { cu += u[0]; cd += dv[0]; } else if (M::a(k) == -1) { cu -= u[0]; cd -= dv[0]; }
-                if (M::b(k) == 1) { cu += u[1]; cd += dv[1]; } else if (M::b(k) == -1) { cu -= u[1]; cd -= dv[1]; }
-                if (M::m(k) == 1) { cu += u[2]; cd += dv[2]; } else if (M::m(k) == -1) { cu -= u[2]; cd -= dv[2]; }
-                const R e0 = wk * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
-                const R de = wk * (R(3) * cd + R(4.5) * cd * (R(2) * cu + cd) - R(1.5) * dsq);
-                const R fv = Store<S, R>::load(src, (size_t)k * nn + n, wk * p.rho_ref);
-                const R fo = fv + p.omega * (rho * e0 - fv) + rho * de;
-                R ho = hv[k] + p.omega_E * (E * e0 - hv[k]) + hv[k] * dEoverE;
-                if (p.pseudoforce) ho += E * de;
-                // push to x + c_k, or bounce back at a wall on the march axis
-                const bool bounce = (M::m(k) == -1 && wall_lo) || (M::m(k) == 1 && wall_hi);
-                const int ko = bounce ? opposite(k) : k;
-                int to = n;
-                if (!bounce) {
-                    if (M::a(k) == 1) to += dA_p; else if (M::a(k) == -1) to += dA_m;
-                    if (M::b(k) == 1) to += dB_p; else if (M::b(k) == -1) to += dB_m;
-                    if (M::m(k) == 1) to += dM_p; else if (M::m(k) == -1) to += dM_m;
-                }
-                // opposite directions share a weight, so the FP16 shift of slot ko is w_k ref
-                Store<S, R>::store(dst, (size_t)ko * nn + to, fo, wk * p.rho_ref);
-                Store<S, R>::store(dst, (size_t)(Q + ko) * nn + to, ho, wk * p.E_ref);
-            }
-        }
     }
 }
 

@@ -172,6 +172,30 @@ const char* lbm_launch_name(const lbm_handle* h, int j);
 /* Free all device state.  NULL is allowed. */
 void lbm_destroy(lbm_handle* h);
 
+/* The paper has no counterpart to this call: it is library plumbing for
+ * callers that cannot allocate device memory, either because all their
+ * device memory belongs to another framework's pool or because an allocation
+ * would synchronise the device and stall their other work.
+ *
+ * Computes the FP64 Kahan sums of lbm_diagnostics (sums[0] mass, sums[1..3]
+ * momentum x, y, z, sums[4] internal energy) of a population buffer the
+ * caller owns, without allocating: `populations` is device memory holding
+ * the 2Q planes of a state in `storage` format, laid out as lbm_get_state
+ * writes them after its 16-byte header (N_0..N_{Q-1}, g_0..g_{Q-1}, each
+ * nx*ny*nz values, x fastest); rho_ref and E_ref are the FP16 shifts (used
+ * only with LBM_STORE_FP16).  `sums` is device memory for 5 doubles, written
+ * asynchronously on `stream` (NULL: default stream); the caller synchronises.
+ *
+ * Scratch: a fixed 40,960-byte array in the library image, held by every
+ * device that loads the library until exit.  The first call on a device
+ * looks up that array's device address (with the device current) and should
+ * come before any stream capture.  Calls share the array, so calls whose
+ * kernels overlap on the GPU race; each call overwrites every partial it
+ * reads.  Rejects null pointers, unknown lattice or storage, and sizes of
+ * 2^31 nodes or more (LBM_ERR_INVALID_ARG); launch failures give LBM_ERR_CUDA. */
+int lbm_conservation_sums_noalloc(int lattice, int storage, int nx, int ny, int nz, double rho_ref,
+                                  double E_ref, const void* populations, double* sums, void* stream);
+
 /* Message of the last error on this thread ("" if none). */
 const char* lbm_last_error(void);
 

@@ -96,6 +96,10 @@ def load(path: str = LIB_PATH):
     lib.lbm_launch_name.restype = ctypes.c_char_p
     lib.lbm_destroy.argtypes = [H]
     lib.lbm_destroy.restype = None
+    lib.lbm_conservation_sums_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.lbm_conservation_sums_noalloc.restype = ctypes.c_int
     lib.lbm_last_error.argtypes = []
     lib.lbm_last_error.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_init", "lbm_step", "lbm_moments", "lbm_diagnostics", "lbm_get_state",
@@ -223,6 +227,17 @@ def lbm_launch_name(h, j: int) -> str:
 def lbm_destroy(h):
     if h:
         load().lbm_destroy(h)
+
+
+def lbm_conservation_sums_noalloc(lattice: int, storage: int, nx: int, ny: int, nz: int, rho_ref: float,
+                                  E_ref: float, populations_ptr: int, sums_ptr: int, stream: int = 0):
+    """Conservation sums of a caller-owned device population buffer, for callers
+    that cannot allocate device memory (the library uses a static scratch
+    array instead).  Pointers are device addresses; the call is asynchronous
+    on `stream`."""
+    return _check(load().lbm_conservation_sums_noalloc(int(lattice), int(storage), int(nx), int(ny), int(nz),
+                                                       float(rho_ref), float(E_ref), ctypes.c_void_p(populations_ptr),
+                                                       ctypes.c_void_p(sums_ptr), ctypes.c_void_p(stream)))
 
 
 class Lbm:

@@ -28,6 +28,7 @@ template <typename R> KParams<R> make_kparams(const lbm_handle* h) {
     const bool shifted = q.storage == LBM_STORE_FP16;
     k.rho_ref = shifted ? (R)q.rho_ref : R(0);
     k.E_ref = shifted ? (R)q.E_ref : R(0);
+    k.step = (unsigned)h->steps;
     return k;
 }
 
@@ -93,16 +94,18 @@ template <int Q, typename S, typename R> struct Impl {
     }
 
     static int step(lbm_handle* h, int n) {
-        const KParams<R> kp = make_kparams<R>(h);
+        KParams<R> kp = make_kparams<R>(h);
         const int L = launches(h);
-        for (int s = 0; s < n; ++s)
+        for (int s = 0; s < n; ++s) {
+            kp.step = (unsigned)(h->steps + s);
             for (int j = 0; j < L; ++j) launch(h, kp, j);
+        }
         return cuda_error(cudaGetLastError(), "lbm_step launch");
     }
 
     // n steps with an event pair around every launch; ms[j] = mean duration of launch j
     static int profile(lbm_handle* h, int n, double* ms, int cap) {
-        const KParams<R> kp = make_kparams<R>(h);
+        KParams<R> kp = make_kparams<R>(h);
         const int L = launches(h);
         cudaEvent_t ev[6];
         for (int e = 0; e < 2 * L; ++e)
@@ -110,6 +113,7 @@ template <int Q, typename S, typename R> struct Impl {
         double acc[3] = {0.0, 0.0, 0.0};
         int rc = LBM_OK;
         for (int s = 0; s < n && !rc; ++s) {
+            kp.step = (unsigned)(h->steps + s);
             for (int j = 0; j < L; ++j) {
                 cudaEventRecord(ev[2 * j], h->stream);
                 launch(h, kp, j);
@@ -129,7 +133,8 @@ template <int Q, typename S, typename R> struct Impl {
     }
 
     static int init(lbm_handle* h, const double* rho, const double* u, const double* eps) {
-        const KParams<R> kp = make_kparams<R>(h);
+        KParams<R> kp = make_kparams<R>(h);
+        kp.step = 0xFFFFFFFFu;   // rounding seed of the initial state, distinct from every step
         init_kernel<Q, S, R><<<grid_for(h->nn, 256), 256, 0, h->stream>>>((S*)h->pop[h->cur], rho, u, eps, kp,
                                                                            (Counters*)h->cnt);
         return cuda_error(cudaGetLastError(), "lbm_init launch");

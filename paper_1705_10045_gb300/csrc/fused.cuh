@@ -264,6 +264,7 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         const R fN = R(1) - om, fG = R(1) - omE + dEoverE;
         const R pf = p->pseudoforce ? R(1) : R(0);
 
+        const unsigned nbits = Store<S, R>::kStochastic ? node_bits(p->step, (unsigned)n) : 0u;
         auto emit = [&](int k, R e0, R de, R fv, R hvk) {
             const R fo = fv * fN + rho * (om * e0 + de);
             const R ho = hvk * fG + E * (omE * e0 + pf * de);
@@ -278,8 +279,8 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
             }
             // opposite directions share a weight, so the FP16 shift of slot ko is w_k ref
             const R wk = R(V::w(k));
-            Store<S, R>::store(dst, (size_t)ko * nn + to, fo, wk * p->rho_ref);
-            Store<S, R>::store(dst, (size_t)(Q + ko) * nn + to, ho, wk * p->E_ref);
+            Store<S, R>::store(dst, (size_t)ko * nn + to, fo, wk * p->rho_ref, slot_bits(nbits, k));
+            Store<S, R>::store(dst, (size_t)(Q + ko) * nn + to, ho, wk * p->E_ref, slot_bits(nbits, Q + k));
         };
         {
             const R w0 = R(V::w(0));

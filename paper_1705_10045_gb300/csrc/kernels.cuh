@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(256) collide_kernel(const S* __restrict__ src,
 
     const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const R dsq = du[0] * (R(2) * u[0] + du[0]) + du[1] * (R(2) * u[1] + du[1]) + du[2] * (R(2) * u[2] + du[2]);
+    const unsigned nbits = Store<S, R>::kStochastic ? node_bits(p.step, (unsigned)i) : 0u;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const R wk = R(V::w(k));
@@ -182,8 +183,8 @@ __global__ void __launch_bounds__(256) collide_kernel(const S* __restrict__ src,
         Nb m = neighbour<D>(x, y, z, V::cx(k), V::cy(k), V::cz(k), p.nx, p.ny, p.nz, p.wall);
         const int ko = m.ghost ? opposite(k) : k;
         const long long to = m.ghost ? i : m.n;
-        Store<S, R>::store(dst, (size_t)ko * nn + to, fs, R(V::w(ko)) * p.rho_ref);
-        Store<S, R>::store(dst, (size_t)(Q + ko) * nn + to, hs, R(V::w(ko)) * p.E_ref);
+        Store<S, R>::store(dst, (size_t)ko * nn + to, fs, R(V::w(ko)) * p.rho_ref, slot_bits(nbits, k));
+        Store<S, R>::store(dst, (size_t)(Q + ko) * nn + to, hs, R(V::w(ko)) * p.E_ref, slot_bits(nbits, Q + k));
     }
 }
 
@@ -215,13 +216,14 @@ __global__ void __launch_bounds__(256) init_kernel(S* __restrict__ pop, const do
         if (dpdrho > R(4.0 / 3.0) || chi >= R(0.5) / R(V::D)) atomicAdd(&cnt->unstable, 1ull);
     }
     const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const unsigned nbits = Store<S, R>::kStochastic ? node_bits(p.step, (unsigned)i) : 0u;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const R wk = R(V::w(k));
         const R cu = cdot<Q, R>(k, u[0], u[1], u[2]);
         const R e0 = wk * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
-        Store<S, R>::store(pop, (size_t)k * nn + i, rho * e0, wk * p.rho_ref);
-        Store<S, R>::store(pop, (size_t)(Q + k) * nn + i, E * e0, wk * p.E_ref);
+        Store<S, R>::store(pop, (size_t)k * nn + i, rho * e0, wk * p.rho_ref, slot_bits(nbits, k));
+        Store<S, R>::store(pop, (size_t)(Q + k) * nn + i, E * e0, wk * p.E_ref, slot_bits(nbits, Q + k));
     }
 }
 

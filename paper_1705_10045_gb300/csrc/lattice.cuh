@@ -65,26 +65,58 @@ __host__ __device__ constexpr int opposite(int k) { return k == 0 ? 0 : ((k & 1)
 
 // ---------------------------------------------------------------------------
 // Storage formats of the population sets.  FP16 stores the shifted value
-// f - w_k * ref (ref = rho_ref for N, E_ref for g), rounded to nearest even.
+// f - w_k * ref (ref = rho_ref for N, E_ref for g) with stochastic rounding:
+// a node that keeps nearly the same populations step after step would
+// otherwise round the same way every step, and round-to-nearest then drifts
+// the mass and energy linearly in time.  The 13 random bits added below the
+// FP16 mantissa come from a counter-based hash of (step, node, slot), so a
+// run is reproducible bit for bit and resumes exactly from a checkpoint.
+
+// "lowbias32" integer hash (C. Wellons' published 32-bit mixer)
+__host__ __device__ __forceinline__ unsigned mix32(unsigned x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// per-node random word of one step; the bits of slot s are the top bits of
+// node_bits * (2s + 1) * golden ratio constant
+__device__ __forceinline__ unsigned node_bits(unsigned step, unsigned n) {
+    return mix32(n * 0x9E3779B1u ^ mix32(step + 0x632BE5ABu));
+}
+__device__ __forceinline__ unsigned slot_bits(unsigned nb, int slot) {
+    return (nb * ((2u * (unsigned)slot + 1u) * 0x9E3779B9u)) >> 19;
+}
 
 template <typename S, typename R> struct Store;
 
 template <> struct Store<double, double> {
+    static constexpr bool kStochastic = false;
     __device__ static double load(const double* p, size_t i, double) { return p[i]; }
-    __device__ static void store(double* p, size_t i, double v, double) { p[i] = v; }
+    __device__ static void store(double* p, size_t i, double v, double, unsigned = 0) { p[i] = v; }
 };
 
 template <> struct Store<float, float> {
+    static constexpr bool kStochastic = false;
     __device__ static float load(const float* p, size_t i, float) { return __ldg(p + i); }
-    __device__ static void store(float* p, size_t i, float v, float) { p[i] = v; }
+    __device__ static void store(float* p, size_t i, float v, float, unsigned = 0) { p[i] = v; }
 };
 
 template <> struct Store<__half, float> {
+    static constexpr bool kStochastic = true;
     __device__ static float load(const __half* p, size_t i, float shift) {
         return __half2float(__ldg(p + i)) + shift;
     }
-    __device__ static void store(__half* p, size_t i, float v, float shift) {
-        p[i] = __float2half_rn(v - shift);
+    // rnd13: 13 random bits; adding them below the 10 FP16 mantissa bits of
+    // the FP32 value and truncating rounds the magnitude up with probability
+    // equal to the discarded fraction (unbiased for FP16-normal values)
+    __device__ static void store(__half* p, size_t i, float v, float shift, unsigned rnd13 = 0) {
+        unsigned b = __float_as_uint(v - shift);
+        b = (b + (rnd13 & 0x1FFFu)) & ~0x1FFFu;
+        p[i] = __float2half_rz(__uint_as_float(b));
     }
 };
 
@@ -106,6 +138,7 @@ template <typename R> struct KParams {
     R T_lo, T_hi;
     int pressure_work, conduction, pseudoforce;
     R rho_ref, E_ref;     // FP16 shifts
+    unsigned step;        // step counter, seeds the FP16 stochastic rounding
 };
 
 // reduced van der Waals EOS scaled by kappa (Sec. 3); T0 when barotropic (Sec. 4)

@@ -249,3 +249,19 @@ def test_heated_wall_steady_conduction(Q):
     z = np.arange(n) + 0.5
     want = 0.85 + (0.75 - 0.85) * z / n
     np.testing.assert_allclose(prof, want, atol=3e-4)
+
+
+def test_laplace_law_pressure_jump_scales_as_one_over_radius():
+    """Resting drops of radius 24 and 32 (128x128, T = 0.7, barotropic): the
+    bulk pressure jump times R is the same within 5 % (Laplace law).  The
+    paper prints no surface tension, so its absolute value is unpinned."""
+    n, prods = 128, []
+    for R in (24.0, 32.0):
+        f = W.moving_droplet_2d(n=n, T=0.7, radius=R, ux=0.0, noise=0.0, hot_dT=0.0)
+        p = oracle.Params(Q=9, nx=n, ny=n, barotropic=True, T0=0.7, lam=0.02)
+        s = oracle.State(p, f.rho, f.u, p.c_v * f.T).step(4000)
+        P = s.moments()["P"].reshape(n, n)
+        dP = P[n // 2, n // 2] - P[0, 0]
+        assert dP > 0
+        prods.append(dP * R)
+    assert max(prods) / min(prods) - 1 < 0.05, prods

@@ -172,6 +172,70 @@ const char* lbm_launch_name(const lbm_handle* h, int j);
 /* Free all device state.  NULL is allowed. */
 void lbm_destroy(lbm_handle* h);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent domains (different sizes, same lattice and
+ * storage) advanced together.  One kernel launch per step covers every
+ * domain through a table of (domain, tile, chunk) work items; runs of 32
+ * launches are captured in a CUDA graph and replayed.  Each domain keeps its
+ * own state in its own device memory and has a step budget: lbm_batch_step(n)
+ * advances every domain by min(n, its remaining budget) steps, so jobs with
+ * different step counts share launches.  Results are bitwise identical to
+ * running each domain alone with lbm_step (the per-node arithmetic is the
+ * same kernel code).  The paper has no counterpart: this is the batched form
+ * of its per-step update for many simulation jobs. */
+typedef struct lbm_batch lbm_batch;
+
+/* Device memory in bytes a domain with parameters *p needs (admission control). */
+size_t lbm_domain_bytes(const lbm_params* p);
+
+/* New empty batch for common->lattice and common->storage on common->device.
+ * Work is enqueued on common->stream, or on a stream the batch creates when
+ * it is NULL (graphs cannot be captured on the legacy default stream). */
+int lbm_batch_create(const lbm_params* common, lbm_batch** out);
+
+/* Create a domain with parameters *p (lattice and storage must match the
+ * batch; stream and device are the batch's), initialise it from rho, u, eps
+ * as lbm_init does, give it a budget of `steps` steps and return its slot id.
+ * Errors as lbm_create and lbm_init (LBM_ERR_OOM when memory runs out). */
+int lbm_batch_add(lbm_batch* b, const lbm_params* p, const double* rho, const double* u, const double* eps,
+                  int mem, long long steps, int* id);
+
+/* Destroy a domain and free its slot (synchronising). */
+int lbm_batch_remove(lbm_batch* b, int id);
+
+/* Enqueue n step launches; every domain takes min(n, budget) steps. */
+int lbm_batch_step(lbm_batch* b, int n);
+
+/* Steps a domain has taken since its initialisation and steps left in its budget. */
+int lbm_batch_status(const lbm_batch* b, int id, long long* steps_done, long long* steps_left);
+
+/* Set a domain's remaining budget. */
+int lbm_batch_set_budget(lbm_batch* b, int id, long long steps);
+
+/* The domain's handle, borrowed for lbm_moments, lbm_diagnostics,
+ * lbm_get_state, lbm_sync (not lbm_destroy or lbm_step); NULL for a bad id. */
+lbm_handle* lbm_batch_domain(lbm_batch* b, int id);
+
+/* Number of domains in the batch. */
+int lbm_batch_size(const lbm_batch* b);
+
+/* CTA shapes the batch kernel can run with, their names, and selection. */
+int lbm_batch_variants(const lbm_batch* b);
+const char* lbm_batch_variant_name(const lbm_batch* b, int v);
+int lbm_batch_set_variant(lbm_batch* b, int v);
+
+/* Autotune: time `reps` launches of every CTA shape on the batch's current
+ * domains (each launch writes a step into the spare buffers and leaves the
+ * state and counters unchanged), keep the fastest, write its index to *best
+ * and the mean ms per launch of shape v to ms[v] (ms may be NULL). */
+int lbm_batch_tune(lbm_batch* b, int reps, int* best, double* ms);
+
+/* Wait for the batch's work; returns a latched device error of any domain. */
+int lbm_batch_sync(lbm_batch* b);
+
+/* Destroy every domain and the batch.  NULL is allowed. */
+void lbm_batch_destroy(lbm_batch* b);
+
 /* The paper has no counterpart to this call: it is library plumbing for
  * callers that cannot allocate device memory, either because all their
  * device memory belongs to another framework's pool or because an allocation

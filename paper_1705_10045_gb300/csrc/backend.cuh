@@ -42,6 +42,19 @@ template <typename R> struct FusedTile<9, R> { static constexpr int TX = 64, TY 
 template <> struct FusedTile<19, float> { static constexpr int TX = 32, TY = 8, NP = 160; };
 template <> struct FusedTile<19, double> { static constexpr int TX = 32, TY = 8, NP = 256; };
 
+// CTA shapes a batch may run with (TX x TY consumers + NP producers); the
+// autotuner times each on the batch and keeps the fastest.
+template <int Q, typename R, int V> struct BatchShape;
+template <typename R> struct BatchShape<9, R, 0> { static constexpr int TX = 64, TY = 1, NP = 64; };
+template <typename R> struct BatchShape<9, R, 1> { static constexpr int TX = 32, TY = 1, NP = 32; };
+template <typename R> struct BatchShape<9, R, 2> { static constexpr int TX = 128, TY = 1, NP = 64; };
+template <> struct BatchShape<19, float, 0> { static constexpr int TX = 32, TY = 8, NP = 160; };
+template <> struct BatchShape<19, float, 1> { static constexpr int TX = 32, TY = 8, NP = 128; };
+template <> struct BatchShape<19, float, 2> { static constexpr int TX = 32, TY = 4, NP = 64; };
+template <> struct BatchShape<19, double, 0> { static constexpr int TX = 32, TY = 8, NP = 256; };
+template <> struct BatchShape<19, double, 1> { static constexpr int TX = 32, TY = 8, NP = 128; };
+template <> struct BatchShape<19, double, 2> { static constexpr int TX = 32, TY = 4, NP = 64; };
+
 template <int Q, typename S, typename R> struct Impl {
     static constexpr int TX = FusedTile<Q, R>::TX, TY = FusedTile<Q, R>::TY, NP = FusedTile<Q, R>::NP;
 
@@ -148,6 +161,73 @@ template <int Q, typename S, typename R> struct Impl {
         output_kernel<Q, R><<<g, 256, 0, h->stream>>>(fld, kp, rho, u, T, P);
         return cuda_error(cudaGetLastError(), "lbm_moments launch");
     }
+    // ---- batches ---------------------------------------------------------
+    // CTA shapes a batch can run with; the autotuner picks one per batch
+    template <int V> struct Shape;
+    static constexpr int kVariants = 3;
+
+    template <int BTX, int BTY, int BNP>
+    static MarchGeom batch_geometry(const lbm_handle* h) {
+        MarchGeom G;
+        G.na = h->p.nx;
+        G.nb = Q == 9 ? 1 : h->p.ny;
+        G.nm = Q == 9 ? h->p.ny : h->p.nz;
+        // chunks of 16 planes keep many CTAs per domain without much ring overlap
+        G.chunk = G.nm < 16 ? G.nm : 16;
+        return G;
+    }
+
+    template <int BTX, int BTY, int BNP>
+    static int build_shape(lbm_batch* b) {
+        std::vector<BatchItem> items;
+        DomainDesc<R>* descs = (DomainDesc<R>*)b->h_descs;
+        for (size_t d = 0; d < b->doms.size(); ++d) {
+            lbm_handle* h = b->doms[d];
+            DomainDesc<R> dd{};
+            if (h) {
+                dd.kp = make_kparams<R>(h);
+                dd.G = batch_geometry<BTX, BTY, BNP>(h);
+                dd.pop[0] = h->pop[0];
+                dd.pop[1] = h->pop[1];
+                dd.cnt = (Counters*)h->cnt;
+                dd.cur = h->cur;
+                dd.left = 0;
+                const int tx = (dd.G.na + BTX - 1) / BTX, ty = (dd.G.nb + BTY - 1) / BTY;
+                const int tz = (dd.G.nm + dd.G.chunk - 1) / dd.G.chunk;
+                for (int z = 0; z < tz; ++z)
+                    for (int y = 0; y < ty; ++y)
+                        for (int x = 0; x < tx; ++x) items.push_back({(int)d, x * BTX, y * BTY, z * dd.G.chunk});
+            }
+            descs[d] = dd;
+        }
+        if (items.size() > b->items_cap) {
+            cudaFree(b->d_items);
+            b->d_items = nullptr;
+            b->items_cap = 0;
+            if (int rc = cuda_error(cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size()), "batch table")) return rc;
+            b->items_cap = items.size();
+        }
+        b->n_items = (int)items.size();
+        if (!items.empty())
+            if (int rc = cuda_error(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(),
+                                                    cudaMemcpyHostToDevice, b->stream), "batch table copy"))
+                return rc;
+        auto kern = fused_batch_kernel<Q, S, R, BTX, BTY, BNP>;
+        const size_t smem = FusedShape<BTX, BTY>::template smem_bytes<R>();
+        return cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                          "batch kernel attribute");
+    }
+
+    template <int BTX, int BTY, int BNP>
+    static void launch_shape(lbm_batch* b, int s) {
+        const size_t smem = FusedShape<BTX, BTY>::template smem_bytes<R>();
+        fused_batch_kernel<Q, S, R, BTX, BTY, BNP><<<b->n_items, BTX * BTY + BNP, smem, b->stream>>>(
+            (const BatchItem*)b->d_items, (const DomainDesc<R>*)b->d_descs, s);
+    }
+
+    static int batch_build(lbm_batch* b);
+    static int batch_launch(lbm_batch* b, int s);
+
     static int reduce(lbm_handle* h, double* out_dev) {
         const KParams<R> kp = make_kparams<R>(h);
         reduce_kernel<Q, S, R><<<kReduceBlocks, kReduceThreads, 0, h->stream>>>((const S*)h->pop[h->cur], kp,
@@ -156,6 +236,40 @@ template <int Q, typename S, typename R> struct Impl {
         return cuda_error(cudaGetLastError(), "lbm_diagnostics launch");
     }
 };
+
+// descriptor bookkeeping after a replay of n launches: every domain took
+// min(n, left) steps
+template <typename R> __global__ void batch_advance_kernel(DomainDesc<R>* doms, int count, int n) {
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < count; d += gridDim.x * blockDim.x) {
+        const int taken = doms[d].left < n ? doms[d].left : n;
+        doms[d].cur ^= taken & 1;
+        doms[d].kp.step += (unsigned)taken;
+        doms[d].left -= taken;
+    }
+}
+
+template <int Q, typename S, typename R> int Impl<Q, S, R>::batch_build(lbm_batch* b) {
+    switch (b->variant) {
+        case 0: return build_shape<BatchShape<Q, R, 0>::TX, BatchShape<Q, R, 0>::TY, BatchShape<Q, R, 0>::NP>(b);
+        case 1: return build_shape<BatchShape<Q, R, 1>::TX, BatchShape<Q, R, 1>::TY, BatchShape<Q, R, 1>::NP>(b);
+        default: return build_shape<BatchShape<Q, R, 2>::TX, BatchShape<Q, R, 2>::TY, BatchShape<Q, R, 2>::NP>(b);
+    }
+}
+
+template <int Q, typename S, typename R> int Impl<Q, S, R>::batch_launch(lbm_batch* b, int s) {
+    if (s >= 0 && b->n_items > 0) {
+        switch (b->variant) {
+            case 0: launch_shape<BatchShape<Q, R, 0>::TX, BatchShape<Q, R, 0>::TY, BatchShape<Q, R, 0>::NP>(b, s); break;
+            case 1: launch_shape<BatchShape<Q, R, 1>::TX, BatchShape<Q, R, 1>::TY, BatchShape<Q, R, 1>::NP>(b, s); break;
+            default: launch_shape<BatchShape<Q, R, 2>::TX, BatchShape<Q, R, 2>::TY, BatchShape<Q, R, 2>::NP>(b, s); break;
+        }
+    }
+    if (s < 0) {   // s < 0: descriptor advance after a replay of -s launches
+        const int count = (int)b->doms.size();
+        batch_advance_kernel<R><<<(count + 127) / 128, 128, 0, b->stream>>>((DomainDesc<R>*)b->d_descs, count, -s);
+    }
+    return cuda_error(cudaGetLastError(), "batch launch");
+}
 
 #define LBM_DISPATCH(h, CALL)                                                   \
     switch ((h)->p.storage) {                                                   \
@@ -184,6 +298,27 @@ template <int Q> int Backend<Q>::moments(lbm_handle* h, double* rho, double* u, 
     LBM_DISPATCH(h, moments(h, rho, u, T, P));
 }
 template <int Q> int Backend<Q>::reduce(lbm_handle* h, double* out_dev) { LBM_DISPATCH(h, reduce(h, out_dev)); }
+#define LBM_BATCH_DISPATCH(b, CALL)                                              \
+    switch ((b)->common.storage) {                                               \
+        case LBM_STORE_FP64: return Impl<Q, double, double>::CALL;               \
+        case LBM_STORE_FP32: return Impl<Q, float, float>::CALL;                 \
+        case LBM_STORE_FP16: return Impl<Q, __half, float>::CALL;                \
+        default: set_error("unknown storage format"); return LBM_ERR_INVALID_ARG; \
+    }
+template <int Q> int Backend<Q>::batch_variants() { return 3; }
+template <int Q> const char* Backend<Q>::batch_variant_name(int v) {
+    static const char* n9[] = {"64x1+64", "32x1+32", "128x1+64"};
+    static const char* n19[] = {"32x8+160", "32x8+128", "32x4+64"};
+    if (v < 0 || v > 2) return "";
+    return Q == 9 ? n9[v] : n19[v];
+}
+template <int Q> int Backend<Q>::batch_build(lbm_batch* b) { LBM_BATCH_DISPATCH(b, batch_build(b)); }
+template <int Q> int Backend<Q>::batch_launch(lbm_batch* b, int s) { LBM_BATCH_DISPATCH(b, batch_launch(b, s)); }
+template <int Q> size_t Backend<Q>::desc_bytes(int storage) {
+    return storage == LBM_STORE_FP64 ? sizeof(DomainDesc<double>) : sizeof(DomainDesc<float>);
+}
+#undef LBM_BATCH_DISPATCH
+
 template <int Q> size_t Backend<Q>::field_bytes(int storage) {
     return (size_t)F_COUNT * (storage == LBM_STORE_FP64 ? sizeof(double) : sizeof(float));
 }

@@ -98,6 +98,7 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
     MarchGeom G;
     size_t nn;
     int plane_n;
+    unsigned step;   // step counter of this launch (seeds FP16 stochastic rounding)
 
     __device__ R& phi(int slot, int r) const { return phis[slot * R_ + r]; }
     __device__ R& rut(int slot, int f, int r) const { return ruts[(slot * Sh::kRut + f) * F_ + r]; }
@@ -264,7 +265,7 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         const R fN = R(1) - om, fG = R(1) - omE + dEoverE;
         const R pf = p->pseudoforce ? R(1) : R(0);
 
-        const unsigned nbits = Store<S, R>::kStochastic ? node_bits(p->step, (unsigned)n) : 0u;
+        const unsigned nbits = Store<S, R>::kStochastic ? node_bits(step, (unsigned)n) : 0u;
         auto emit = [&](int k, R e0, R de, R fv, R hvk) {
             const R fo = fv * fN + rho * (om * e0 + de);
             const R ho = hvk * fG + E * (omE * e0 + pf * de);
@@ -303,15 +304,16 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
     }
 };
 
-// Producer/consumer fused step.  Threads [0, TX*TY) are consumers (one per
+// One CTA of the producer/consumer fused step: the tile (a0, b0) of planes
+// [zb, zb + G.chunk) of one domain.  Threads [0, TX*TY) are consumers (one per
 // tile node), threads [TX*TY, TX*TY + NP) producers.
 template <int Q, typename S, typename R, int TX, int TY, int NP>
-__global__ void __launch_bounds__(TX* TY + NP) fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst,
-                                                                 KParams<R> p, MarchGeom G, Counters* cnt) {
+__device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restrict__ dst, const KParams<R>* p,
+                                           const MarchGeom& G, unsigned step, int a0, int b0, int zb,
+                                           Counters* cnt, unsigned char* smem_raw) {
     using St = FusedStages<Q, S, R, TX, TY>;
     using Sh = typename St::Sh;
     constexpr int NC = TX * TY, NT = NC + NP;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     St st;
     st.phis = reinterpret_cast<R*>(smem_raw);
     st.ruts = st.phis + Sh::kPhiSlots * Sh::R;
@@ -320,16 +322,15 @@ __global__ void __launch_bounds__(TX* TY + NP) fused_step_kernel(const S* __rest
     st.ring_b = st.ring_a + Sh::RW;
     st.src = src;
     st.dst = dst;
-    st.p = &p;
+    st.p = p;
     st.G = G;
-    st.nn = (size_t)p.nn;
+    st.nn = (size_t)p->nn;
     st.plane_n = G.na * G.nb;
+    st.step = step;
 
     const int tid = threadIdx.x;
-    const int a0 = blockIdx.x * TX, b0 = blockIdx.y * TY;
-    const int zb = blockIdx.z * G.chunk;
     const int ze = min(zb + G.chunk, G.nm);
-    const bool walls = p.wall;
+    const bool walls = p->wall;
     for (int i = tid; i < Sh::RW; i += NT) st.ring_a[i] = wrapi(a0 + i - 2, G.na);
     for (int i = tid; i < Sh::RH; i += NT) st.ring_b[i] = wrapi(b0 + i - Sh::RB, G.nb) * G.na;
 
@@ -358,6 +359,51 @@ __global__ void __launch_bounds__(TX* TY + NP) fused_step_kernel(const S* __rest
         }
         __syncthreads();
     }
+}
+
+// Single-domain fused step: CTA (x, y, z) takes tile (x TX, y TY) and the
+// z-th chunk of planes.
+template <int Q, typename S, typename R, int TX, int TY, int NP>
+__global__ void __launch_bounds__(TX* TY + NP) fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                                                                 KParams<R> p, MarchGeom G, Counters* cnt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fused_tile<Q, S, R, TX, TY, NP>(src, dst, &p, G, p.step, blockIdx.x * TX, blockIdx.y * TY,
+                                    blockIdx.z * G.chunk, cnt, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Many domains in one launch.  Every CTA reads its work item (domain, tile,
+// chunk) from a table and the domain's descriptor; s is the step index within
+// a sequence of launches: a domain takes part while s < left and reads the
+// buffer (cur + s) mod 2.
+
+struct BatchItem {
+    int domain, a0, b0, zb;
+};
+
+template <typename R> struct DomainDesc {
+    KParams<R> kp;      // kp.step: the domain's step count at s = 0
+    MarchGeom G;
+    void* pop[2];
+    Counters* cnt;
+    int cur;            // buffer holding the state at s = 0
+    int left;           // steps the domain still takes, counted from s = 0
+};
+
+template <int Q, typename S, typename R, int TX, int TY, int NP>
+__global__ void __launch_bounds__(TX* TY + NP) fused_batch_kernel(const BatchItem* __restrict__ items,
+                                                                  const DomainDesc<R>* __restrict__ doms, int s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ KParams<R> kp;   // the domain's parameters, read once per CTA
+    const BatchItem it = items[blockIdx.x];
+    const DomainDesc<R>* d = doms + it.domain;
+    if (s >= d->left) return;   // the whole CTA leaves: its domain is done
+    if (threadIdx.x == 0) kp = d->kp;
+    const int in = (d->cur + s) & 1;
+    const MarchGeom G = d->G;
+    __syncthreads();
+    fused_tile<Q, S, R, TX, TY, NP>((const S*)d->pop[in], (S*)d->pop[in ^ 1], &kp, G, kp.step + (unsigned)s, it.a0,
+                                    it.b0, it.zb, d->cnt, smem_raw);
 }
 
 }  // namespace lbm

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 
@@ -24,7 +25,30 @@ struct lbm_handle {
     cudaStream_t stream = nullptr;
 };
 
+// Many domains advanced together (lbm_batch_*): every domain is an
+// lbm_handle; one launch per step covers all of them through a work table.
+struct lbm_batch {
+    lbm_params common;
+    int Q = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;            // created by lbm_batch_create
+    std::vector<lbm_handle*> doms;      // slot -> domain handle (nullptr: free slot)
+    std::vector<long long> budget;      // steps each domain may still take
+    void* d_items = nullptr;            // BatchItem[items_cap]
+    size_t items_cap = 0;
+    int n_items = 0;
+    void* d_descs = nullptr;            // DomainDesc<R>[descs_cap]
+    void* h_descs = nullptr;            // pinned staging of the descriptors
+    size_t descs_cap = 0;
+    bool dirty = true;                  // work table out of date
+    int variant = 0;                    // CTA shape (see lbm_batch_variants)
+    cudaGraphExec_t graph = nullptr;    // kGraphLaunches launches, s = 0..kGraphLaunches-1
+    int graph_items = -1, graph_variant = -1;
+};
+
 namespace lbm {
+
+constexpr int kGraphLaunches = 32;
 
 // error reporting shared by the translation units
 void set_error(const std::string& msg);
@@ -40,6 +64,12 @@ template <int Q> struct Backend {
     static int moments(lbm_handle* h, double* rho, double* u, double* T, double* P);       // device pointers
     static int reduce(lbm_handle* h, double* out_dev);   // 5 sums into device memory
     static size_t field_bytes(int storage);
+    // batches: shapes, work table, descriptors and one launch of step s
+    static int batch_variants();
+    static const char* batch_variant_name(int v);
+    static int batch_build(lbm_batch* b);
+    static int batch_launch(lbm_batch* b, int s);
+    static size_t desc_bytes(int storage);
 };
 
 }  // namespace lbm

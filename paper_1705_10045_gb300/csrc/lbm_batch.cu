@@ -1,0 +1,391 @@
+// Batches of domains advanced together (lbm_batch_* in include/lbm.h).
+//
+// Every domain is an ordinary lbm_handle (own population buffers, counters
+// and moments scratch), created on the batch's stream.  One launch per step
+// covers all domains through a table of work items (domain, tile, chunk);
+// each domain's descriptor in device memory holds its pointers, parameters,
+// the buffer holding its state and the steps it still takes in the current
+// request.  Runs of kGraphLaunches launches plus a descriptor-advance kernel
+// are captured once into a CUDA graph and replayed; there are no spin waits
+// between CTAs, the kernel boundaries order the steps.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fused.cuh"
+#include "internal.h"
+
+using lbm::cuda_error;
+using lbm::set_error;
+
+namespace {
+
+int be_build(lbm_batch* b) { return b->Q == 9 ? lbm::Backend<9>::batch_build(b) : lbm::Backend<19>::batch_build(b); }
+int be_launch(lbm_batch* b, int s) {
+    return b->Q == 9 ? lbm::Backend<9>::batch_launch(b, s) : lbm::Backend<19>::batch_launch(b, s);
+}
+size_t be_desc_bytes(const lbm_batch* b) {
+    return b->Q == 9 ? lbm::Backend<9>::desc_bytes(b->common.storage) : lbm::Backend<19>::desc_bytes(b->common.storage);
+}
+
+int check_batch(const lbm_batch* b) {
+    if (!b) {
+        set_error("null batch");
+        return LBM_ERR_INVALID_ARG;
+    }
+    return LBM_OK;
+}
+
+int check_slot(const lbm_batch* b, int id) {
+    if (id < 0 || (size_t)id >= b->doms.size() || !b->doms[id]) {
+        set_error("no domain with id " + std::to_string(id) + " in this batch");
+        return LBM_ERR_INVALID_ARG;
+    }
+    return LBM_OK;
+}
+
+void drop_graph(lbm_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_items = b->graph_variant = -1;
+}
+
+// Descriptor storage for every slot (device array + pinned staging).
+int ensure_descs(lbm_batch* b) {
+    const size_t need = std::max<size_t>(b->doms.size(), 1);
+    if (need <= b->descs_cap) return LBM_OK;
+    const size_t cap = std::max<size_t>(need, 2 * b->descs_cap);
+    const size_t bytes = cap * be_desc_bytes(b);
+    void *d = nullptr, *h = nullptr;
+    if (int rc = cuda_error(cudaMalloc(&d, bytes), "batch descriptors")) return rc;
+    if (int rc = cuda_error(cudaMallocHost(&h, bytes), "batch descriptor staging")) {
+        cudaFree(d);
+        return rc;
+    }
+    std::memset(h, 0, bytes);
+    if (b->d_descs) {
+        cudaStreamSynchronize(b->stream);
+        cudaFree(b->d_descs);
+        cudaFreeHost(b->h_descs);
+    }
+    b->d_descs = d;
+    b->h_descs = h;
+    b->descs_cap = cap;
+    drop_graph(b);   // the graph baked the old descriptor address
+    return LBM_OK;
+}
+
+// Work table for the current slots and shape; descriptors restaged.
+int rebuild(lbm_batch* b) {
+    if (int rc = cudaStreamSynchronize(b->stream)) return cuda_error((cudaError_t)rc, "batch synchronize");
+    if (int rc = ensure_descs(b)) return rc;
+    if (int rc = be_build(b)) return rc;
+    b->dirty = false;
+    return LBM_OK;
+}
+
+// Host copy of the per-domain descriptor fields that change between requests:
+// the buffer holding the state, the step counter and the steps to take.
+template <typename R> void stage_descs(lbm_batch* b, long long n) {
+    auto* dd = (lbm::DomainDesc<R>*)b->h_descs;
+    for (size_t d = 0; d < b->doms.size(); ++d) {
+        lbm_handle* h = b->doms[d];
+        if (!h) {
+            dd[d].left = 0;
+            continue;
+        }
+        dd[d].cur = h->cur;
+        dd[d].kp.step = (unsigned)h->steps;
+        dd[d].left = (int)std::min<long long>(b->budget[d], n);
+    }
+}
+
+int upload_descs(lbm_batch* b, long long n) {
+    if (b->common.storage == LBM_STORE_FP64) stage_descs<double>(b, n);
+    else stage_descs<float>(b, n);
+    return cuda_error(cudaMemcpyAsync(b->d_descs, b->h_descs, b->doms.size() * be_desc_bytes(b), cudaMemcpyHostToDevice,
+                                      b->stream),
+                      "batch descriptor copy");
+}
+
+int capture_graph(lbm_batch* b) {
+    cudaGraph_t g = nullptr;
+    if (int rc = cuda_error(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture"))
+        return rc;
+    int rc = LBM_OK;
+    for (int s = 0; s < lbm::kGraphLaunches && !rc; ++s) rc = be_launch(b, s);
+    if (!rc) rc = be_launch(b, -lbm::kGraphLaunches);
+    const int rc_end = cuda_error(cudaStreamEndCapture(b->stream, &g), "graph capture end");
+    if (rc || rc_end) {
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : rc_end;
+    }
+    rc = cuda_error(cudaGraphInstantiate(&b->graph, g, 0), "graph instantiate");
+    cudaGraphDestroy(g);
+    if (rc) return rc;
+    b->graph_items = b->n_items;
+    b->graph_variant = b->variant;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_domain_bytes(const lbm_params* p) {
+    if (!p || (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19)) return 0;
+    const size_t nn = (size_t)p->nx * p->ny * p->nz;
+    const size_t elem = p->storage == LBM_STORE_FP64 ? 8 : (p->storage == LBM_STORE_FP32 ? 4 : 2);
+    const size_t fields = p->lattice == LBM_D2Q9 ? lbm::Backend<9>::field_bytes(p->storage)
+                                                 : lbm::Backend<19>::field_bytes(p->storage);
+    // two population buffers of 2Q planes, the moments fields, reduction and counter scratch
+    return 2 * 2 * (size_t)p->lattice * nn * elem + fields * nn +
+           sizeof(double) * (lbm::kSums * lbm::kReduceBlocks + 8) + sizeof(lbm::Counters);
+}
+
+int lbm_batch_create(const lbm_params* common, lbm_batch** out) {
+    if (!common || !out) {
+        set_error("lbm_batch_create: null argument");
+        return LBM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (common->lattice != LBM_D2Q9 && common->lattice != LBM_D3Q19) {
+        set_error("lattice must be LBM_D2Q9 or LBM_D3Q19");
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (common->storage < LBM_STORE_FP64 || common->storage > LBM_STORE_FP16) {
+        set_error("unknown storage format");
+        return LBM_ERR_INVALID_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || common->device < 0 || common->device >= ndev) {
+        set_error("no CUDA device with ordinal " + std::to_string(common->device));
+        return LBM_ERR_CUDA;
+    }
+    cudaSetDevice(common->device);
+    lbm_batch* b = new lbm_batch();
+    b->common = *common;
+    b->Q = common->lattice;
+    // graphs cannot be captured on the legacy default stream: own one when none is given
+    if (common->stream) {
+        b->stream = (cudaStream_t)common->stream;
+    } else if (int rc = cuda_error(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "batch stream")) {
+        delete b;
+        return rc;
+    } else {
+        b->own_stream = true;
+    }
+    b->common.stream = b->stream;
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_add(lbm_batch* b, const lbm_params* p, const double* rho, const double* u, const double* eps, int mem,
+                  long long steps, int* id) {
+    if (int rc = check_batch(b)) return rc;
+    if (!p || !id || steps < 0) {
+        set_error("lbm_batch_add: null parameters or id, or steps < 0");
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (p->lattice != b->common.lattice || p->storage != b->common.storage) {
+        set_error("lbm_batch_add: a domain must have the batch's lattice and storage");
+        return LBM_ERR_INVALID_ARG;
+    }
+    lbm_params q = *p;
+    q.stream = b->stream;
+    q.device = b->common.device;
+    q.step_kernel = LBM_STEP_FUSED;
+    lbm_handle* h = nullptr;
+    if (int rc = lbm_create(&q, &h)) return rc;
+    if (int rc = lbm_init(h, rho, u, eps, mem)) {
+        lbm_destroy(h);
+        return rc;
+    }
+    size_t slot = 0;
+    while (slot < b->doms.size() && b->doms[slot]) ++slot;
+    if (slot == b->doms.size()) {
+        b->doms.push_back(nullptr);
+        b->budget.push_back(0);
+    }
+    b->doms[slot] = h;
+    b->budget[slot] = steps;
+    b->dirty = true;
+    *id = (int)slot;
+    return LBM_OK;
+}
+
+int lbm_batch_remove(lbm_batch* b, int id) {
+    if (int rc = check_batch(b)) return rc;
+    if (int rc = check_slot(b, id)) return rc;
+    cudaStreamSynchronize(b->stream);
+    lbm_destroy(b->doms[id]);
+    b->doms[id] = nullptr;
+    b->budget[id] = 0;
+    b->dirty = true;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int n) {
+    if (int rc = check_batch(b)) return rc;
+    if (n < 0) {
+        set_error("lbm_batch_step: n < 0");
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (n == 0) return LBM_OK;
+    cudaSetDevice(b->common.device);
+    if (b->dirty)
+        if (int rc = rebuild(b)) return rc;
+    // the pinned staging may still feed the previous request's copy
+    if (int rc = cuda_error(cudaStreamSynchronize(b->stream), "batch synchronize")) return rc;
+    if (int rc = upload_descs(b, n)) return rc;
+    const int full = n / lbm::kGraphLaunches, rem = n % lbm::kGraphLaunches;
+    if (full > 0 && (!b->graph || b->graph_items != b->n_items || b->graph_variant != b->variant)) {
+        drop_graph(b);
+        if (int rc = capture_graph(b)) return rc;
+    }
+    for (int r = 0; r < full; ++r)
+        if (int rc = cuda_error(cudaGraphLaunch(b->graph, b->stream), "graph launch")) return rc;
+    for (int s = 0; s < rem; ++s)
+        if (int rc = be_launch(b, s)) return rc;
+    if (rem > 0)
+        if (int rc = be_launch(b, -rem)) return rc;
+    // host mirrors follow the same arithmetic as the device descriptors
+    for (size_t d = 0; d < b->doms.size(); ++d) {
+        lbm_handle* h = b->doms[d];
+        if (!h) continue;
+        const long long taken = std::min<long long>(b->budget[d], n);
+        h->cur ^= (int)(taken & 1);
+        h->steps += taken;
+        b->budget[d] -= taken;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_status(const lbm_batch* b, int id, long long* steps_done, long long* steps_left) {
+    if (int rc = check_batch(b)) return rc;
+    if (int rc = check_slot(b, id)) return rc;
+    if (steps_done) *steps_done = b->doms[id]->steps;
+    if (steps_left) *steps_left = b->budget[id];
+    return LBM_OK;
+}
+
+int lbm_batch_set_budget(lbm_batch* b, int id, long long steps) {
+    if (int rc = check_batch(b)) return rc;
+    if (int rc = check_slot(b, id)) return rc;
+    if (steps < 0) {
+        set_error("lbm_batch_set_budget: steps < 0");
+        return LBM_ERR_INVALID_ARG;
+    }
+    b->budget[id] = steps;
+    return LBM_OK;
+}
+
+lbm_handle* lbm_batch_domain(lbm_batch* b, int id) {
+    if (!b || check_slot(b, id)) return nullptr;
+    return b->doms[id];
+}
+
+int lbm_batch_size(const lbm_batch* b) {
+    if (!b) return 0;
+    int n = 0;
+    for (auto* h : b->doms) n += h != nullptr;
+    return n;
+}
+
+int lbm_batch_variants(const lbm_batch* b) {
+    if (!b) return 0;
+    return b->Q == 9 ? lbm::Backend<9>::batch_variants() : lbm::Backend<19>::batch_variants();
+}
+
+const char* lbm_batch_variant_name(const lbm_batch* b, int v) {
+    if (!b) return "";
+    return b->Q == 9 ? lbm::Backend<9>::batch_variant_name(v) : lbm::Backend<19>::batch_variant_name(v);
+}
+
+int lbm_batch_set_variant(lbm_batch* b, int v) {
+    if (int rc = check_batch(b)) return rc;
+    if (v < 0 || v >= lbm_batch_variants(b)) {
+        set_error("lbm_batch_set_variant: no such CTA shape");
+        return LBM_ERR_INVALID_ARG;
+    }
+    b->variant = v;
+    b->dirty = true;
+    return LBM_OK;
+}
+
+int lbm_batch_tune(lbm_batch* b, int reps, int* best, double* ms) {
+    if (int rc = check_batch(b)) return rc;
+    if (reps < 1) {
+        set_error("lbm_batch_tune: reps < 1");
+        return LBM_ERR_INVALID_ARG;
+    }
+    cudaSetDevice(b->common.device);
+    // one step of every domain from its current buffer into the other one
+    // leaves the state untouched; the counters are restored afterwards
+    std::vector<lbm::Counters> saved(b->doms.size());
+    if (int rc = cuda_error(cudaStreamSynchronize(b->stream), "batch synchronize")) return rc;
+    for (size_t d = 0; d < b->doms.size(); ++d)
+        if (b->doms[d]) cudaMemcpy(&saved[d], b->doms[d]->cnt, sizeof(lbm::Counters), cudaMemcpyDeviceToHost);
+    const int nv = lbm_batch_variants(b);
+    int best_v = b->variant;
+    double best_ms = 1e30;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = LBM_OK;
+    for (int v = 0; v < nv && !rc; ++v) {
+        b->variant = v;
+        if ((rc = rebuild(b))) break;
+        std::vector<long long> keep = b->budget;
+        for (auto& x : b->budget) x = 1;
+        if ((rc = upload_descs(b, 1))) break;
+        b->budget = keep;
+        rc = be_launch(b, 0);   // warm-up
+        cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps && !rc; ++r) rc = be_launch(b, 0);
+        cudaEventRecord(e1, b->stream);
+        if (!rc) rc = cuda_error(cudaEventSynchronize(e1), "tune synchronize");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        const double per = t / reps;
+        if (ms) ms[v] = per;
+        if (per < best_ms) {
+            best_ms = per;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (size_t d = 0; d < b->doms.size(); ++d)
+        if (b->doms[d]) cudaMemcpy(b->doms[d]->cnt, &saved[d], sizeof(lbm::Counters), cudaMemcpyHostToDevice);
+    b->variant = best_v;
+    b->dirty = true;
+    drop_graph(b);
+    if (best) *best = best_v;
+    return rc;
+}
+
+int lbm_batch_sync(lbm_batch* b) {
+    if (int rc = check_batch(b)) return rc;
+    int rc = LBM_OK;
+    for (auto* h : b->doms)
+        if (h && !rc) rc = lbm_sync(h);
+    if (!rc) rc = cuda_error(cudaStreamSynchronize(b->stream), "batch synchronize");
+    return rc;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->common.device);
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    for (auto* h : b->doms) lbm_destroy(h);
+    cudaFree(b->d_items);
+    cudaFree(b->d_descs);
+    cudaFreeHost(b->h_descs);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

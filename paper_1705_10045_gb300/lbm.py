@@ -38,7 +38,11 @@ LBM_STEP_THREE_LAUNCH = 1
 
 EXPORTED = ("lbm_default_params", "lbm_create", "lbm_init", "lbm_step", "lbm_moments", "lbm_diagnostics",
             "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_sync", "lbm_launches_per_step",
-            "lbm_profile_step", "lbm_launch_name", "lbm_destroy", "lbm_last_error")
+            "lbm_profile_step", "lbm_launch_name", "lbm_destroy", "lbm_last_error", "lbm_domain_bytes",
+            "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_status",
+            "lbm_batch_set_budget", "lbm_batch_domain", "lbm_batch_size", "lbm_batch_variants",
+            "lbm_batch_variant_name", "lbm_batch_set_variant", "lbm_batch_tune", "lbm_batch_sync",
+            "lbm_batch_destroy", "lbm_conservation_sums_noalloc")
 
 
 class LbmError(RuntimeError):
@@ -104,6 +108,31 @@ def load(path: str = LIB_PATH):
     lib.lbm_last_error.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_init", "lbm_step", "lbm_moments", "lbm_diagnostics", "lbm_get_state",
                  "lbm_set_state", "lbm_sync", "lbm_launches_per_step"):
+        getattr(lib, name).restype = ctypes.c_int
+    B = ctypes.c_void_p
+    LL = ctypes.c_longlong
+    lib.lbm_domain_bytes.argtypes = [P]
+    lib.lbm_domain_bytes.restype = ctypes.c_size_t
+    lib.lbm_batch_create.argtypes = [P, ctypes.POINTER(B)]
+    lib.lbm_batch_add.argtypes = [B, P, dp, dp, dp, ctypes.c_int, LL, ctypes.POINTER(ctypes.c_int)]
+    lib.lbm_batch_remove.argtypes = [B, ctypes.c_int]
+    lib.lbm_batch_step.argtypes = [B, ctypes.c_int]
+    lib.lbm_batch_status.argtypes = [B, ctypes.c_int, ctypes.POINTER(LL), ctypes.POINTER(LL)]
+    lib.lbm_batch_set_budget.argtypes = [B, ctypes.c_int, LL]
+    lib.lbm_batch_domain.argtypes = [B, ctypes.c_int]
+    lib.lbm_batch_domain.restype = H
+    lib.lbm_batch_size.argtypes = [B]
+    lib.lbm_batch_variants.argtypes = [B]
+    lib.lbm_batch_variant_name.argtypes = [B, ctypes.c_int]
+    lib.lbm_batch_variant_name.restype = ctypes.c_char_p
+    lib.lbm_batch_set_variant.argtypes = [B, ctypes.c_int]
+    lib.lbm_batch_tune.argtypes = [B, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    lib.lbm_batch_sync.argtypes = [B]
+    lib.lbm_batch_destroy.argtypes = [B]
+    lib.lbm_batch_destroy.restype = None
+    for name in ("lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_status",
+                 "lbm_batch_set_budget", "lbm_batch_size", "lbm_batch_variants", "lbm_batch_set_variant",
+                 "lbm_batch_tune", "lbm_batch_sync"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -283,6 +312,100 @@ class Lbm:
         if getattr(self, "h", None):
             lbm_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lbm_domain_bytes(params: lbm_params) -> int:
+    return int(load().lbm_domain_bytes(ctypes.byref(params)))
+
+
+class LbmBatch:
+    """Many domains advanced together by one launch per step (lbm_batch_*)."""
+
+    def __init__(self, **common):
+        self.common = make_params(**common)
+        b = ctypes.c_void_p()
+        _check(load().lbm_batch_create(ctypes.byref(self.common), ctypes.byref(b)))
+        self.b = b
+        self.shapes = {}
+
+    def add(self, rho, u, eps, steps: int, **kw) -> int:
+        """Add a domain (keywords as for Lbm; lattice and storage default to the batch's)."""
+        kw.setdefault("lattice", self.common.lattice)
+        kw.setdefault("storage", self.common.storage)
+        p = make_params(**kw)
+        (r, m1), (uu, m2), (e, m3) = _addr(rho), _addr(u), _addr(eps)
+        if not (m1 == m2 == m3):
+            raise ValueError("rho, u and eps must all live on the host or all on the device")
+        i = ctypes.c_int()
+        _check(load().lbm_batch_add(self.b, ctypes.byref(p), r, uu, e, m1, int(steps), ctypes.byref(i)))
+        self.shapes[i.value] = (p.nz, p.ny, p.nx)
+        return i.value
+
+    def remove(self, i: int):
+        _check(load().lbm_batch_remove(self.b, int(i)))
+        self.shapes.pop(i, None)
+
+    def step(self, n: int):
+        return _check(load().lbm_batch_step(self.b, int(n)))
+
+    def status(self, i: int) -> tuple:
+        done, left = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load().lbm_batch_status(self.b, int(i), ctypes.byref(done), ctypes.byref(left)))
+        return done.value, left.value
+
+    def set_budget(self, i: int, steps: int):
+        return _check(load().lbm_batch_set_budget(self.b, int(i), int(steps)))
+
+    def handle(self, i: int):
+        h = load().lbm_batch_domain(self.b, int(i))
+        if not h:
+            raise LbmError(LBM_ERR_INVALID_ARG, load().lbm_last_error().decode())
+        return ctypes.c_void_p(h)
+
+    def moments(self, i: int) -> dict:
+        nz, ny, nx = self.shapes[i]
+        d = 2 if self.common.lattice == LBM_D2Q9 else 3
+        out = {"rho": np.empty((nz, ny, nx)), "u": np.empty((d, nz, ny, nx)), "T": np.empty((nz, ny, nx)),
+               "P": np.empty((nz, ny, nx))}
+        lbm_moments(self.handle(i), out["rho"], out["u"], out["T"], out["P"])
+        return out
+
+    def diagnostics(self, i: int) -> np.ndarray:
+        return lbm_diagnostics(self.handle(i))
+
+    def get_state(self, i: int) -> np.ndarray:
+        return lbm_get_state(self.handle(i))
+
+    def size(self) -> int:
+        return int(load().lbm_batch_size(self.b))
+
+    def variants(self) -> list:
+        return [load().lbm_batch_variant_name(self.b, v).decode() for v in range(load().lbm_batch_variants(self.b))]
+
+    def set_variant(self, v: int):
+        return _check(load().lbm_batch_set_variant(self.b, int(v)))
+
+    def tune(self, reps: int = 3) -> tuple:
+        """Autotune the CTA shape; returns (best index, ms per launch of every shape)."""
+        nv = load().lbm_batch_variants(self.b)
+        ms = (ctypes.c_double * nv)()
+        best = ctypes.c_int()
+        _check(load().lbm_batch_tune(self.b, int(reps), ctypes.byref(best), ms))
+        return best.value, list(ms)
+
+    def sync(self):
+        return _check(load().lbm_batch_sync(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().lbm_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

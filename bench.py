@@ -189,6 +189,125 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _digest(res: dict) -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for k in ("rho", "u", "T", "P"):
+        h.update(np.ascontiguousarray(res[k]).tobytes())
+    return h.hexdigest()
+
+
+BATCH_STEPS = 5000
+
+
+def batched_bench(count: int = 256, steps: int = BATCH_STEPS):
+    """Many uneven D2Q9 droplet domains, FP32: square sides uniform in
+    {64, 96, ..., 512}, T uniform in [0.7, 0.95], radius uniform in
+    [8, side/4], +-1e-3 noise, constant thermal diffusivity 0.05 (a constant
+    conductivity would break the explicit limit in the thinnest vapour at
+    T = 0.7), `steps` steps each.  Batched arm: one LbmBatch
+    (add every domain from host fields, autotune the CTA shape, advance all
+    domains together, copy every domain's moments to the host).  Plain arm:
+    the same jobs one after another through lbm_create/lbm_init/lbm_step/
+    lbm_moments.  Both timed end to end on the host clock; each job's moments
+    are compared bit for bit between the arms."""
+    import torch
+    from paper_1705_10045_gb300 import lbm
+    from paper_1705_10045_gb300 import workloads as W
+    jobs = W.batched_droplet_jobs(count)
+    kw = dict(lattice=9, storage=lbm.LBM_STORE_FP32, chi_mode=1, chi=0.05)
+    inputs = []
+    for j in jobs:
+        f = W.droplet_2d(j["side"], j["T"], j["radius"], noise=1e-3, seed=j["seed"])
+        inputs.append((f.rho, np.ascontiguousarray(f.u), 1.5 * f.T))
+    nodes = sum(j["side"] ** 2 for j in jobs)
+    torch.cuda.synchronize()
+
+    t0 = time.perf_counter()
+    b = lbm.LbmBatch(**kw)
+    ids = [b.add(rho, u, eps, steps, nx=j["side"], ny=j["side"], chi_mode=1, chi=0.05)
+           for j, (rho, u, eps) in zip(jobs, inputs)]
+    best, tune_ms = b.tune(reps=3)
+    b.sync()
+    t1 = time.perf_counter()
+    b.step(steps)
+    b.sync()
+    t2 = time.perf_counter()
+    got = [_digest(b.moments(i)) for i in ids]
+    b.close()
+    t3 = time.perf_counter()
+    batched_s = t3 - t0
+
+    t0 = time.perf_counter()
+    ref = []
+    for j, (rho, u, eps) in zip(jobs, inputs):
+        sim = lbm.Lbm(nx=j["side"], ny=j["side"], **kw)
+        sim.init(rho, u, eps)
+        sim.step(steps)
+        ref.append(_digest(sim.moments()))
+        sim.close()
+    plain_s = time.perf_counter() - t0
+    variants = lbm.LbmBatch(**kw)
+    names = variants.variants()
+    variants.close()
+    return {
+        "workload": f"{count} D2Q9 droplet domains, sides 64..512 step 32 ({nodes} nodes), T in [0.7, 0.95], "
+                    f"radius in [8, side/4], +-1e-3 noise, chi=0.05, FP32, {steps} steps each",
+        "metric": "jobs/s", "value": count / batched_s, "plain_value": count / plain_s,
+        "speedup_vs_plain": plain_s / batched_s, "batched_s": batched_s, "plain_s": plain_s,
+        "batched_step_s": t2 - t1, "batched_step_mlups": nodes * steps / (t2 - t1) / 1e6,
+        "tuned_variant": names[best], "tune_ms_per_launch": dict(zip(names, tune_ms)),
+        "bitwise_equal_to_plain": got == ref,
+        "timing": "host clock, end to end: host fields in, autotune, all steps, moments of every job out",
+    }
+
+
+def serving_bench(count: int = 24, storage: int = None, seed: int = 5):
+    """Serving stream: Poisson arrivals at 200 jobs/s of D3Q19 droplet/slab
+    cubes, sides uniform in [32, 192], steps uniform in [500, 5000], T in
+    [0.7, 0.9], constant thermal diffusivity 0.05, FP32 storage (FP16 when
+    asked); the first `count` arrivals of the trace.  Served by continuous
+    batching (Server) and by plain sequential runs in arrival order; each
+    request carries its initial fields (built before the clock starts)."""
+    from paper_1705_10045_gb300 import lbm
+    from paper_1705_10045_gb300 import serve
+    from paper_1705_10045_gb300 import workloads as W
+    storage = lbm.LBM_STORE_FP32 if storage is None else storage
+    trace = W.serving_trace(count=count, rate=200.0, seed=seed)
+
+    def jobs():
+        out = serve.trace_jobs(trace)
+        for j in out:
+            data = j.fields()
+            j.fields = (lambda d=data: d)
+        return out
+
+    served = jobs()
+    srv = serve.Server(lbm.LBM_D3Q19, storage)
+    try:
+        st = srv.run(served)
+    finally:
+        srv.close()
+    a = {j.name: _digest(j.result) for j in served}
+    del served
+    plain = jobs()
+    sq = serve.run_sequential(plain, lbm.LBM_D3Q19, storage)
+    b = {j.name: _digest(j.result) for j in plain}
+    del plain
+    return {
+        "workload": f"first {count} arrivals of a Poisson trace at 200 jobs/s: D3Q19 droplet/slab cubes, side "
+                    f"32..192, steps 500..5000, T in [0.7, 0.9], chi=0.05, "
+                    f"{'FP16 shifted' if storage == lbm.LBM_STORE_FP16 else 'FP32'} storage",
+        "metric": "jobs/s", "value": st.jobs_per_s, "p50_s": st.p50_s, "p99_s": st.p99_s,
+        "plain_value": sq.jobs_per_s, "plain_p50_s": sq.p50_s, "plain_p99_s": sq.p99_s,
+        "speedup_vs_plain": st.jobs_per_s / sq.jobs_per_s, "p99_vs_plain": st.p99_s / sq.p99_s,
+        "mlups": st.mlups, "plain_mlups": sq.mlups, "max_resident": st.max_resident,
+        "peak_device_bytes": st.peak_bytes, "wall_s": st.wall_s, "plain_wall_s": sq.wall_s,
+        "bitwise_equal_to_plain": a == b,
+        "timing": "host clock from the first arrival; latency = results on the host minus arrival",
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -196,6 +315,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-domains measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
+    ap.add_argument("--serve-jobs", type=int, default=24)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -301,6 +423,10 @@ def main():
             "diagnostics": {"mass": diag["mass"], "energy": diag["energy"], "clamps": diag["clamps"],
                             "bad": diag["bad"]},
         }
+        if ws == 1 and not args.no_batched:
+            line["batched"] = batched_bench()
+        if ws == 1 and not args.no_serving:
+            line["serving"] = serving_bench(args.serve_jobs)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

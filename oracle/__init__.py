@@ -52,6 +52,7 @@ class _Params(ctypes.Structure):
         ("wall", ctypes.c_int), ("T_fixed_lo", ctypes.c_int), ("T_fixed_hi", ctypes.c_int),
         ("T_lo", ctypes.c_double), ("T_hi", ctypes.c_double),
         ("pressure_work", ctypes.c_int), ("conduction", ctypes.c_int), ("pseudoforce", ctypes.c_int),
+        ("latent", ctypes.c_double), ("coex", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -81,6 +82,7 @@ class Params:
     pressure_work: bool = True
     conduction: bool = True
     pseudoforce: bool = True
+    latent: float = 0.0      # rho_liq Q of Sec. 5; 0 switches the latent heat off
 
     @property
     def d(self) -> int:
@@ -95,9 +97,30 @@ class Params:
         for name, _ in _Params._fields_:
             if name == "g":
                 c.g = (ctypes.c_double * 3)(*[float(v) for v in self.g])
+            elif name == "coex":
+                c.coex = _ptr(coexistence_table())
             else:
                 setattr(c, name, type(getattr(c, name))(getattr(self, name)))
         return c
+
+
+_COEX = None
+
+
+def coexistence_table() -> np.ndarray:
+    """Maxwell densities on the grid T_j = 0.5 + j/1024, j = 0..512, as one
+    array [rho_v(T_0..T_512), rho_l(T_0..T_512)] (the table the C oracle
+    interpolates in for the latent-heat source of Sec. 5)."""
+    global _COEX
+    if _COEX is None:
+        from . import maxwell
+        n = 512
+        tab = np.ones(2 * (n + 1))
+        for j in range(n):
+            rv, rl, _ = maxwell.coexistence(0.5 + j / 1024.0)
+            tab[j], tab[n + 1 + j] = rv, rl
+        _COEX = tab
+    return _COEX
 
 
 def lib():

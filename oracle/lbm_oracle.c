@@ -40,7 +40,17 @@ typedef struct {
     int T_fixed_lo, T_fixed_hi;   /* wall temperature mode: 0 adiabatic, 1 fixed */
     double T_lo, T_hi;
     int pressure_work, conduction, pseudoforce;   /* physics switches */
+    double latent;       /* rho_liq Q of Sec. 5 (energy per volume); 0: no latent heat */
+    const double* coex;  /* Maxwell densities on the temperature grid below:
+                            coex[j] = rho_v(T_j), coex[LH_N + 1 + j] = rho_l(T_j) */
 } orc_params;
+
+/* Temperature grid of the coexistence table used by the latent-heat source:
+ * T_j = LH_T0 + j / LH_PER_T, j = 0..LH_N (the last point is the critical
+ * point, where rho_v = rho_l = 1). */
+#define LH_T0 0.5
+#define LH_PER_T 1024.0
+#define LH_N 512
 
 /* ---------------------------------------------------------------------- */
 /* Velocity sets, Sec. 2: rest vector, nearest neighbours, next-nearest.
@@ -236,13 +246,37 @@ static double conductivity(const orc_params* p, double rho)
     return p->chi_mode ? rho * p->c_v * p->chi : p->lambda;
 }
 
+/* Vapour and liquid densities on the coexistence curve at temperature T, by
+ * linear interpolation in the table (T below the grid takes its first
+ * point).  Returns 0 at or above the critical temperature (no two-phase
+ * band), 1 otherwise. */
+static int coexistence_at(const orc_params* p, double T, double* rv, double* rl)
+{
+    if (!(T < 1.0)) return 0;
+    double s = (T - LH_T0) * LH_PER_T;
+    if (s < 0.0) s = 0.0;
+    int j = (int)floor(s);
+    if (j > LH_N - 1) j = LH_N - 1;
+    double f = s - (double)j;
+    const double* v = p->coex;
+    const double* l = p->coex + LH_N + 1;
+    *rv = v[j] + f * (v[j + 1] - v[j]);
+    *rl = l[j] + f * (l[j + 1] - l[j]);
+    return 1;
+}
+
 /* Step part 3: change of internal energy by finite differences (Sec. 4):
  *   pressure work  -p div(u*) dt, with the centred difference of Sec. 6.2
  *   applied along every axis;
  *   conduction     div(lambda grad T) dt, conservative form with the face
  *   conductivity the mean of the two nodes.
  * Across a wall: u*(ghost) = -u*(mirror) (no-slip), T(ghost) = T(mirror)
- * for an adiabatic wall and 2 T_w - T(mirror) for a wall held at T_w. */
+ * for an adiabatic wall and 2 T_w - T(mirror) for a wall held at T_w.
+ * Latent heat of the phase transition (Sec. 5), when p->latent = rho_liq Q
+ * is nonzero: inside the transition layer rho_v(T) < rho < rho_l(T) the
+ * energy changes by  (rho_liq Q / (rho_l - rho_v)) d(rho)/dt  with
+ * d(rho)/dt = -rho div(u*), the divergence being the same centred
+ * difference as in the pressure work. */
 void orc_energy_source(const orc_params* p, const double* rho, const double* ustar,
                        const double* T, const double* P, double* dE)
 {
@@ -273,6 +307,11 @@ void orc_energy_source(const orc_params* p, const double* rho, const double* ust
                 double s = 0.0;
                 if (p->pressure_work) s += -P[n] * div;
                 if (p->conduction) s += cond;
+                if (p->latent != 0.0) {
+                    double rv, rl;
+                    if (coexistence_at(p, T[n], &rv, &rl) && rho[n] > rv && rho[n] < rl)
+                        s += -p->latent * rho[n] * div / (rl - rv);
+                }
                 dE[n] = s;
             }
 }

@@ -44,9 +44,23 @@ def _dist():
     return ws, rank, local
 
 
+DEPTH = 64
+
+
+def _set_size(spec: str) -> None:
+    """Rescale the pool-boiling box (NXxNYxNZ, liquid a quarter of the height
+    deep), e.g. for a profiler capture that must stay small."""
+    global NX, NY, NZ, DEPTH, WORKLOAD
+    NX, NY, NZ = (int(v) for v in spec.lower().split("x"))
+    DEPTH = max(4, NZ // 4)
+    PARAMS.update(nx=NX, ny=NY, nz=NZ)
+    WORKLOAD = (f"D3Q19 thermal pool boiling {NX}x{NY}x{NZ}, walls on z (bottom T=0.95 fixed, top adiabatic), "
+                f"liquid {DEPTH} deep at T=0.8, g=-1e-5 z, FP32")
+
+
 def _fields():
     from paper_1705_10045_gb300 import workloads as W
-    return W.pool_boiling_3d(nx=NX, ny=NY, nz=NZ, T=0.8, depth=64, noise=1e-4, seed=3)
+    return W.pool_boiling_3d(nx=NX, ny=NY, nz=NZ, T=0.8, depth=DEPTH, noise=1e-4, seed=3)
 
 
 KERNEL_SOURCES = ("fused.cuh", "kernels.cuh", "lattice.cuh", "backend.cuh")
@@ -318,7 +332,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-domains measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--serve-jobs", type=int, default=24)
+    ap.add_argument("--size", default=None, help="NXxNYxNZ of a smaller pool-boiling box (profiling)")
     args = ap.parse_args()
+    if args.size:
+        _set_size(args.size)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -407,7 +424,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nodes": nn, "l2": "inputs larger than L2 (11.5 GB of population "
+            "config": {"workload": WORKLOAD, "nodes": nn, "l2": f"inputs larger than L2 ({304 * nn / 1e9:.2f} GB of population "
                        "traffic per step vs 129 MB L2), no flush", "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

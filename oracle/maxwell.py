@@ -11,12 +11,17 @@ rho = T = p = 1).  At coexistence the vapour (rho_v) and liquid (rho_l) share
 
 The integral of the vdW isotherm in specific volume has the closed form
     int p~ dv = (8T/3) ln(3v - 1) + 3/v.
-The two conditions are solved by Newton iteration in float64 starting from
-the spinodal bracket.  The result is independent of the lattice pressure scale.
+The saturation pressure is found by bracketed root finding between the two
+spinodal pressures (where dp/drho = 0), with the vapour and liquid volumes
+bracketed on their own branches, so the trivial solution v_l = v_v of the
+two conditions cannot be reached.  The result is independent of the lattice
+pressure scale.
 """
 from __future__ import annotations
 
 import math
+
+from scipy import optimize
 
 
 def p_red(rho: float, T: float) -> float:
@@ -32,43 +37,41 @@ def _int_p_dv(v: float, T: float) -> float:
     return 8.0 * T / 3.0 * math.log(3.0 * v - 1.0) + 3.0 / v
 
 
-def coexistence(T: float, tol: float = 1e-14) -> tuple[float, float, float]:
-    """Return (rho_v, rho_l, p_s) on the Maxwell coexistence curve at 0.3 <= T < 1."""
+def spinodals(T: float) -> tuple[float, float]:
+    """Densities where dp/drho = 0 on the isotherm T < 1 (vapour, liquid):
+    24T/(3 - rho)^2 = 6 rho, i.e. rho (3 - rho)^2 = 4T."""
+    f = lambda r: r * (3.0 - r) ** 2 - 4.0 * T
+    return optimize.brentq(f, 0.0, 1.0, xtol=1e-15), optimize.brentq(f, 1.0, 3.0, xtol=1e-15)
+
+
+def _branches(ps: float, T: float, s_v: float, s_l: float) -> tuple[float, float]:
+    """Vapour and liquid volumes where p~ = ps (outside the spinodal region)."""
+    g = lambda r: p_red(r, T) - ps
+    rv = optimize.brentq(g, 0.0, s_v, xtol=1e-16, rtol=1e-15)
+    rl = optimize.brentq(g, s_l, 3.0 - 1e-12, xtol=1e-16, rtol=1e-15)
+    return 1.0 / rv, 1.0 / rl
+
+
+def coexistence(T: float) -> tuple[float, float, float]:
+    """Return (rho_v, rho_l, p_s) on the Maxwell coexistence curve at 0.3 <= T < 1.
+
+    The saturation pressure p_s is the root, between the two spinodal
+    pressures, of the equal-area residual
+        integral_{v_l}^{v_v} p~ dv - p_s (v_v - v_l),
+    where v_v, v_l are the outer roots of p~(v) = p_s; each root is bracketed."""
     if not (0.3 <= T < 1.0):
         raise ValueError("T must lie in [0.3, 1)")
-    # start from a symmetric guess around the critical density, then Newton
-    # on the two equations in (v_l, v_v)
-    eps = math.sqrt(max(1.0 - T, 1e-12))
-    rl, rv = 1.0 + 2.0 * eps, max(1.0 - 2.0 * eps, 1e-3)
-    if T < 0.85:
-        # low temperature: better guesses from the ideal-gas/liquid limits
-        rl = min(2.9, 1.0 + 2.0 * eps)
-        rv = 0.5 * (1.0 - eps) ** 2
-    vl, vv = 1.0 / rl, 1.0 / rv
-    for _ in range(200):
-        pl = 8.0 * T / (3.0 * vl - 1.0) - 3.0 / vl ** 2
-        pv = 8.0 * T / (3.0 * vv - 1.0) - 3.0 / vv ** 2
-        f1 = pl - pv
-        f2 = (_int_p_dv(vv, T) - _int_p_dv(vl, T)) - 0.5 * (pl + pv) * (vv - vl)
-        dpl = -24.0 * T / (3.0 * vl - 1.0) ** 2 + 6.0 / vl ** 3
-        dpv = -24.0 * T / (3.0 * vv - 1.0) ** 2 + 6.0 / vv ** 3
-        # partial derivatives of f2: d/dvl = -pl - 0.5 dpl (vv-vl) + 0.5 (pl+pv)
-        j11, j12 = dpl, -dpv
-        j21 = -pl - 0.5 * dpl * (vv - vl) + 0.5 * (pl + pv)
-        j22 = pv - 0.5 * dpv * (vv - vl) - 0.5 * (pl + pv)
-        det = j11 * j22 - j12 * j21
-        dvl = (f1 * j22 - f2 * j12) / det
-        dvv = (j11 * f2 - j21 * f1) / det
-        # damp the step so that both volumes stay on their branches
-        lam = 1.0
-        while (vl - lam * dvl <= 1.0 / 3.0 + 1e-12 or vv - lam * dvv <= vl - lam * dvl) and lam > 1e-6:
-            lam *= 0.5
-        vl -= lam * dvl
-        vv -= lam * dvv
-        if abs(dvl) < tol * vl and abs(dvv) < tol * vv:
-            break
-    rl, rv = 1.0 / vl, 1.0 / vv
-    return rv, rl, p_red(rl, T)
+    s_v, s_l = spinodals(T)
+    hi = p_red(s_v, T)
+    lo = max(p_red(s_l, T), 1e-10 * hi)
+
+    def area(ps):
+        vv, vl = _branches(ps, T, s_v, s_l)
+        return (_int_p_dv(vv, T) - _int_p_dv(vl, T)) - ps * (vv - vl)
+
+    ps = optimize.brentq(area, lo, hi, xtol=1e-300, rtol=1e-15, maxiter=500)
+    vv, vl = _branches(ps, T, s_v, s_l)
+    return 1.0 / vv, 1.0 / vl, ps
 
 
 if __name__ == "__main__":

@@ -54,6 +54,24 @@ def test_maxwell_solver_against_quadrature(T):
     assert abs(1 / vl - rl) < 1e-8 and abs(1 / vv - rv) < 1e-8
 
 
+def test_maxwell_definition_holds_on_the_whole_temperature_grid():
+    """Equal pressure and equal chemical potential of the two phases, and
+    both densities outside the spinodal region, at every point of the
+    latent-heat table's grid (T = 0.5 + j/1024).  The chemical potential is
+    written here from the vdW free energy per particle
+    f = -(8T/3) ln(3/rho - 1) - 3 rho: mu = f + p/rho."""
+    def mu(r, T):
+        return -(8 * T / 3) * math.log((3 - r) / r) + 8 * T / (3 - r) - 6 * r
+
+    for j in range(0, 512, 3):
+        T = 0.5 + j / 1024
+        rv, rl, ps = maxwell.coexistence(T)
+        s_v, s_l = maxwell.spinodals(T)
+        assert 0 < rv < s_v < 1.0 < s_l < rl < 3, T
+        assert abs(maxwell.p_red(rv, T) - maxwell.p_red(rl, T)) < 1e-12, T
+        assert abs(mu(rl, T) - mu(rv, T)) < 1e-11, T
+
+
 def test_eos_stability_and_pseudopotential_sign_at_default_scale():
     """With the default lattice pressure scale the vdW isotherms used here
     satisfy the stability criterion of Sec. 3, (dp/drho)_T <= (h/dt)^2 + theta,

@@ -96,12 +96,25 @@ typedef struct lbm_params {
     int pressure_work;    /* include -p div(u*) in dE (Sec. 4) */
     int conduction;       /* include div(lambda grad T) in dE (Sec. 4) */
     int pseudoforce;      /* include the energy pseudoforce (Sec. 4) */
+    double latent;        /* rho_liq Q of Sec. 5, energy per volume in the units of
+                             E = rho c_v T; 0 (default) switches the latent heat off.
+                             When nonzero, dE gains -latent rho div(u*)/(rho_l - rho_v)
+                             at nodes with rho_v(T) < rho < rho_l(T), the Maxwell
+                             densities interpolated linearly in T on the grid
+                             T = 0.5 + j/1024 (j = 0..512; T < 0.5 takes the first
+                             point, T >= 1 has no transition layer) */
     int storage;          /* LBM_STORE_* */
     double rho_ref, E_ref;/* shifts of the FP16 storage (ignored otherwise) */
     int step_kernel;      /* LBM_STEP_FUSED (default) or LBM_STEP_THREE_LAUNCH */
     void* stream;         /* cudaStream_t the library enqueues on (NULL: default stream) */
     int device;           /* CUDA device ordinal */
 } lbm_params;
+
+/* Maxwell coexistence densities of the reduced vdW fluid at 0 < T < 1
+ * (Sec. 3): equal pressure and chemical potential of the two phases.  Host
+ * computation, no device needed.  Returns LBM_OK, or LBM_ERR_INVALID_ARG for
+ * T outside (0, 1) or a null pointer. */
+int lbm_coexistence(double T, double* rho_v, double* rho_l);
 
 /* Fill *p with defaults: D2Q9 64x64x1, kappa 0.01, A -0.152, tau = tau_E = 1,
  * c_v 1.5, lambda 0.05, periodic, all physics switches on, FP32 storage,

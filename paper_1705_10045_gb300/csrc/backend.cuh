@@ -29,6 +29,8 @@ template <typename R> KParams<R> make_kparams(const lbm_handle* h) {
     k.rho_ref = shifted ? (R)q.rho_ref : R(0);
     k.E_ref = shifted ? (R)q.E_ref : R(0);
     k.step = (unsigned)h->steps;
+    k.latent = (R)q.latent;
+    k.coex = (const R*)h->coex;
     return k;
 }
 

@@ -233,6 +233,7 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         R dE = 0;
         if (p->pressure_work) dE += -P * div;
         if (p->conduction) dE += cond;
+        if (p->latent != R(0)) dE += latent_heat(*p, rho, T, div);
         if (P - rho * third >= R(0)) atomicAdd(&cnt->clamps, 1ull);
 
         const int n = c * plane_n + n_ab;

@@ -18,6 +18,7 @@ struct lbm_handle {
     void* cnt = nullptr;        // lbm::Counters on the device
     double* partials = nullptr; // reduction scratch: block partials + 8 results
     double* staging = nullptr;  // (D + 3) planes of doubles for host transfers, allocated on demand
+    void* coex = nullptr;       // coexistence table (arithmetic type) when p.latent != 0
     unsigned long long reported_bad = 0;
     long long steps = 0;
     bool initialised = false;

@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(256) collide_kernel(const S* __restrict__ src,
     R dE = R(0);
     if (p.pressure_work) dE += -eos_pressure(p, rho, T) * div;
     if (p.conduction) dE += cond;
+    if (p.latent != R(0)) dE += latent_heat(p, rho, T, div);
 
     // energy of the node (same summation order as fields_kernel)
     R E = R(0);

@@ -139,6 +139,8 @@ template <typename R> struct KParams {
     int pressure_work, conduction, pseudoforce;
     R rho_ref, E_ref;     // FP16 shifts
     unsigned step;        // step counter, seeds the FP16 stochastic rounding
+    R latent;             // rho_liq Q of Sec. 5 (0: no latent heat)
+    const R* coex;        // rho_v then rho_l on T = 0.5 + j/1024, j = 0..512
 };
 
 // reduced van der Waals EOS scaled by kappa (Sec. 3); T0 when barotropic (Sec. 4)
@@ -151,6 +153,28 @@ __device__ __forceinline__ R eos_pressure(const KParams<R>& p, R rho, R T) {
 template <typename R>
 __device__ __forceinline__ R conductivity(const KParams<R>& p, R rho) {
     return p.chi_mode ? rho * p.c_v * p.chi : p.lambda;
+}
+
+// Latent heat of the phase transition (Sec. 5): inside the transition layer
+// rho_v(T) < rho < rho_l(T) the energy changes by
+//   (rho_liq Q / (rho_l - rho_v)) drho/dt,  drho/dt = -rho div(u*),
+// with the Maxwell densities interpolated linearly in T in the table
+// (T below the grid takes its first point; no layer at T >= 1).  div is the
+// centred-difference divergence of u* the pressure work uses.
+template <typename R>
+__device__ __forceinline__ R latent_heat(const KParams<R>& p, R rho, R T, R div) {
+    if (!(T < R(1))) return R(0);
+    R s = (T - R(0.5)) * R(1024);
+    if (s < R(0)) s = R(0);
+    int j = (int)floor(s);
+    if (j > 511) j = 511;
+    const R f = s - (R)j;
+    const R* v = p.coex;
+    const R* l = p.coex + 513;
+    const R rv = v[j] + f * (v[j + 1] - v[j]);
+    const R rl = l[j] + f * (l[j + 1] - l[j]);
+    if (!(rho > rv && rho < rl)) return R(0);
+    return -p.latent * rho * div / (rl - rv);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,11 +1,14 @@
 // C-ABI of liblbm (declared in include/lbm.h): parameter validation, device
 // memory, host/device transfers, error latching and dispatch to the
 // per-lattice back ends.
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
+#include "coexistence.h"
 #include "internal.h"
 #include "kernels.cuh"
 
@@ -56,6 +59,20 @@ int need_init(const lbm_handle* h) {
         return LBM_ERR_INVALID_ARG;
     }
     return LBM_OK;
+}
+
+// Coexistence table of the latent-heat source in the kernels' arithmetic
+// type: rho_v at the kCoexIntervals + 1 grid temperatures, then rho_l.
+int upload_coexistence(lbm_handle* h) {
+    constexpr int n = lbm::kCoexIntervals + 1;
+    std::vector<double> tab(2 * n);
+    lbm::coexistence_table(tab.data(), tab.data() + n);
+    const bool dbl = h->p.storage == LBM_STORE_FP64;
+    const size_t bytes = (dbl ? sizeof(double) : sizeof(float)) * tab.size();
+    if (int rc = cuda_error(cudaMalloc(&h->coex, bytes), "coexistence table allocation")) return rc;
+    if (dbl) return cuda_error(cudaMemcpy(h->coex, tab.data(), bytes, cudaMemcpyHostToDevice), "coexistence table");
+    std::vector<float> f(tab.begin(), tab.end());
+    return cuda_error(cudaMemcpy(h->coex, f.data(), bytes, cudaMemcpyHostToDevice), "coexistence table");
 }
 
 int ensure_staging(lbm_handle* h) {
@@ -154,6 +171,10 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
         set_error("step_kernel must be LBM_STEP_FUSED or LBM_STEP_THREE_LAUNCH");
         return LBM_ERR_INVALID_ARG;
     }
+    if (!std::isfinite(p->latent)) {
+        set_error("latent must be finite");
+        return LBM_ERR_INVALID_ARG;
+    }
     if (p->chi_mode && p->conduction && !(p->chi < 0.5 / (p->lattice == LBM_D2Q9 ? 2 : 3))) {
         set_error("explicit conduction needs chi < 0.5/d (Sec. 6.1)");
         return LBM_ERR_UNSTABLE_PARAMS;
@@ -186,11 +207,20 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
     if (!rc) rc = cuda_error(cudaMalloc((void**)&h->partials, sizeof(double) * (lbm::kSums * lbm::kReduceBlocks + 8)),
                              "reduction scratch allocation");
     if (!rc) rc = cuda_error(cudaMemsetAsync(h->cnt, 0, sizeof(lbm::Counters), h->stream), "counter reset");
+    if (!rc && p->latent != 0.0) rc = upload_coexistence(h);
     if (rc) {
         lbm_destroy(h);
         return rc;
     }
     *out = h;
+    return LBM_OK;
+}
+
+int lbm_coexistence(double T, double* rho_v, double* rho_l) {
+    if (!rho_v || !rho_l || !lbm::coexistence(T, rho_v, rho_l)) {
+        set_error("lbm_coexistence: need 0 < T < 1 and two output pointers");
+        return LBM_ERR_INVALID_ARG;
+    }
     return LBM_OK;
 }
 
@@ -420,6 +450,7 @@ void lbm_destroy(lbm_handle* h) {
     cudaFree(h->cnt);
     cudaFree(h->partials);
     cudaFree(h->staging);
+    cudaFree(h->coex);
     delete h;
 }
 

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "fused.cuh"
+#include "coexistence.h"
 #include "internal.h"
 
 using lbm::cuda_error;
@@ -140,8 +141,9 @@ size_t lbm_domain_bytes(const lbm_params* p) {
     const size_t fields = p->lattice == LBM_D2Q9 ? lbm::Backend<9>::field_bytes(p->storage)
                                                  : lbm::Backend<19>::field_bytes(p->storage);
     // two population buffers of 2Q planes, the moments fields, reduction and counter scratch
+    const size_t coex = p->latent != 0.0 ? 2 * (size_t)(lbm::kCoexIntervals + 1) * (elem == 8 ? 8 : 4) : 0;
     return 2 * 2 * (size_t)p->lattice * nn * elem + fields * nn +
-           sizeof(double) * (lbm::kSums * lbm::kReduceBlocks + 8) + sizeof(lbm::Counters);
+           sizeof(double) * (lbm::kSums * lbm::kReduceBlocks + 8) + sizeof(lbm::Counters) + coex;
 }
 
 int lbm_batch_create(const lbm_params* common, lbm_batch** out) {

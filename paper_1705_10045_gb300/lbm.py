@@ -42,7 +42,7 @@ EXPORTED = ("lbm_default_params", "lbm_create", "lbm_init", "lbm_step", "lbm_mom
             "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_status",
             "lbm_batch_set_budget", "lbm_batch_domain", "lbm_batch_size", "lbm_batch_variants",
             "lbm_batch_variant_name", "lbm_batch_set_variant", "lbm_batch_tune", "lbm_batch_sync",
-            "lbm_batch_destroy", "lbm_conservation_sums_noalloc")
+            "lbm_batch_destroy", "lbm_conservation_sums_noalloc", "lbm_coexistence")
 
 
 class LbmError(RuntimeError):
@@ -61,6 +61,7 @@ class lbm_params(ctypes.Structure):
         ("wall", ctypes.c_int), ("T_fixed_lo", ctypes.c_int), ("T_fixed_hi", ctypes.c_int),
         ("T_lo", ctypes.c_double), ("T_hi", ctypes.c_double),
         ("pressure_work", ctypes.c_int), ("conduction", ctypes.c_int), ("pseudoforce", ctypes.c_int),
+        ("latent", ctypes.c_double),
         ("storage", ctypes.c_int), ("rho_ref", ctypes.c_double), ("E_ref", ctypes.c_double),
         ("step_kernel", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("device", ctypes.c_int),
@@ -104,6 +105,9 @@ def load(path: str = LIB_PATH):
                                                   ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.lbm_conservation_sums_noalloc.restype = ctypes.c_int
+    lib.lbm_coexistence.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]
+    lib.lbm_coexistence.restype = ctypes.c_int
     lib.lbm_last_error.argtypes = []
     lib.lbm_last_error.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_init", "lbm_step", "lbm_moments", "lbm_diagnostics", "lbm_get_state",
@@ -181,6 +185,13 @@ def make_params(**kw) -> lbm_params:
                 raise AttributeError(f"lbm_params has no field {k}")
             setattr(p, k, int(v) if isinstance(v, bool) else v)
     return p
+
+
+def lbm_coexistence(T: float) -> tuple:
+    """(rho_v, rho_l) on the Maxwell coexistence curve of the reduced vdW fluid."""
+    rv, rl = ctypes.c_double(), ctypes.c_double()
+    _check(load().lbm_coexistence(float(T), ctypes.byref(rv), ctypes.byref(rl)))
+    return rv.value, rl.value
 
 
 def lbm_create(params: lbm_params):

@@ -72,3 +72,18 @@ def test_null_handle_calls_fail_cleanly(libpath):
     assert L.lbm_state_bytes(None) == 0
     L.lbm_destroy(None)
     assert b"null handle" in L.lbm_last_error()
+
+
+def test_host_coexistence_agrees_with_the_oracle_maxwell_solver(libpath):
+    """The library's own coexistence solver (bisection on the pressure until
+    the chemical potentials agree) against the oracle's (equal-area
+    construction) on the grid of the latent-heat table; they share no code."""
+    from oracle import maxwell
+    for j in range(0, 512, 5):
+        T = 0.5 + j / 1024
+        rv, rl = lbm.lbm_coexistence(T)
+        ov, ol, _ = maxwell.coexistence(T)
+        assert abs(rv - ov) <= 1e-11 * ov and abs(rl - ol) <= 1e-11 * ol, T
+    for bad in (0.0, 1.0, 1.2, float("nan")):
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_coexistence(bad)

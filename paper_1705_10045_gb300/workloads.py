@@ -173,6 +173,17 @@ def uniform_gas(shape, rho, T, u=None) -> Fields:
     return Fields(np.full(shape, float(rho)), uu, np.full(shape, float(T)))
 
 
+def spinodal(shape, rho0=0.7, T0=0.8, noise=1e-3, seed=6) -> Fields:
+    """Spinodal decomposition (Sec. 6.2, 6.3): a fluid at rest at uniform
+    density rho0 inside the spinodal region and uniform T0, with seeded
+    +-noise on the density that lets the unstable modes grow.  shape is
+    (nz, ny, nx); nz = 1 for D2Q9, ny = nz = 1 for a row."""
+    shape = tuple(shape)
+    d = 2 if shape[0] == 1 else 3
+    rho = np.full(shape, float(rho0)) + (uniform_noise(shape, noise, seed) if noise else 0.0)
+    return Fields(rho, np.zeros((d,) + shape), np.full(shape, float(T0)))
+
+
 # ---------------------------------------------------------------------------
 # job lists
 

@@ -214,6 +214,36 @@ def _digest(res: dict) -> str:
 BATCH_STEPS = 5000
 
 
+def storage_leg(storage: int, steps: int, rho_h, u_h, eps_h, stream, dev) -> dict:
+    """The headline workload with another population storage format: FP16
+    shifted storage (FP32 arithmetic, 152 B per lattice update) or FP64
+    (608 B per update; FP64 arithmetic)."""
+    import torch
+    from paper_1705_10045_gb300 import lbm
+    sim = lbm.Lbm(storage=storage, device=dev, stream=stream.cuda_stream, **PARAMS)
+    try:
+        sim.init(rho_h, u_h, eps_h)
+        sim.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        diag = sim.diagnostics()
+    finally:
+        sim.close()
+    nn = NX * NY * NZ
+    per_node = {lbm.LBM_STORE_FP16: 152, lbm.LBM_STORE_FP64: 608}[storage]
+    peak, kind = _peak()
+    gbs = per_node * nn / (ms * 1e-3) / 1e9
+    return {"storage": {lbm.LBM_STORE_FP16: "fp16-shifted", lbm.LBM_STORE_FP64: "fp64"}[storage],
+            "value": nn / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": steps,
+            "algorithmic_bytes_per_node": per_node, "achieved_gbs": gbs, "frac": gbs / peak, "peak_kind": kind,
+            "bad_nodes": diag["bad"]}
+
+
 def batched_bench(count: int = 256, steps: int = BATCH_STEPS):
     """Many uneven D2Q9 droplet domains, FP32: square sides uniform in
     {64, 96, ..., 512}, T uniform in [0.7, 0.95], radius uniform in
@@ -331,6 +361,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-domains measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
+    ap.add_argument("--no-storage-legs", action="store_true", help="skip the FP16 and FP64 storage legs")
     ap.add_argument("--serve-jobs", type=int, default=24)
     ap.add_argument("--size", default=None, help="NXxNYxNZ of a smaller pool-boiling box (profiling)")
     args = ap.parse_args()
@@ -409,6 +440,11 @@ def main():
     h2d = (rho_h.numel() + u_h.numel() + eps_h.numel()) * 8
     d2h = sum(v.numel() for v in out.values()) * 8
     sim.close()
+    extra_storage = {}
+    if not args.no_storage_legs:
+        extra_storage["fp16_storage"] = storage_leg(lbm.LBM_STORE_FP16, min(args.steps, 200), rho_h, u_h, eps_h,
+                                                    stream, dev)
+        extra_storage["fp64"] = storage_leg(lbm.LBM_STORE_FP64, min(args.steps, 10), rho_h, u_h, eps_h, stream, dev)
 
     if rank == 0:
         peak, peak_kind = _peak()
@@ -440,6 +476,7 @@ def main():
             "diagnostics": {"mass": diag["mass"], "energy": diag["energy"], "clamps": diag["clamps"],
                             "bad": diag["bad"]},
         }
+        line.update(extra_storage)
         if ws == 1 and not args.no_batched:
             line["batched"] = batched_bench()
         if ws == 1 and not args.no_serving:

@@ -17,9 +17,13 @@
 //      planes earlier), collides N and g and pushes them to x + c_k.
 // The CTA is warp-specialised: producer warps run M on plane i and F on
 // plane i-1 while consumer warps (one thread per tile node) run C on plane
-// i-3, so population loads overlap the collision arithmetic.  One CTA-wide
-// barrier per plane hands the buffers over; a named barrier orders M before
-// F inside the producer warps.  Ring nodes are recomputed by neighbouring
+// i-3 or later, so population loads overlap the collision arithmetic.  The
+// two roles hand planes over through mbarriers in shared memory: producers
+// release iteration i when M(i) and F(i-1) are done, and consumers release
+// plane c when C(c) has read its buffers, which the producers wait for before
+// overwriting them.  Neither role waits for the other's whole iteration, so a
+// slow plane on one side does not stall the other.  A named barrier orders M
+// before F, and F before the next M, inside the producer warps.  Ring nodes are recomputed by neighbouring
 // CTAs from L2 rather than exchanged.  D2Q9 runs the same code as a lattice
 // with one y node: its lattice y axis is the march axis and its tile is
 // TX x 1.
@@ -34,6 +38,30 @@
 #include "kernels.cuh"
 
 namespace lbm {
+
+// mbarrier helpers of the producer/consumer hand-off (shared memory, CTA scope)
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+// Wait until the phase of parity `parity` of *b has completed, for at most
+// about half a second (1e9 clock cycles); false when the wait gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+    const long long t0 = clock64();
+    while (clock64() - t0 < 1000000000ll) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(b)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 // Velocity of direction k in march coordinates: (a, b) across the tile,
 // m along the march axis.
@@ -68,9 +96,16 @@ template <int TX, int TY> struct FusedShape {
     static constexpr int F = FW * FH;
     static constexpr int kRut = 5;                      // rho, ua, ub, um, T
     static constexpr int kPhiSlots = 3, kRutSlots = 5, kDuSlots = 4;
+    static constexpr int kHandSlots = 8;   // mbarrier ring of the producer/consumer hand-off
+    template <typename R_> static constexpr size_t table_offset() {
+        return sizeof(R_) * ((size_t)kPhiSlots * R + (size_t)kRutSlots * kRut * F + (size_t)kDuSlots * 3 * F);
+    }
+    template <typename R_> static constexpr size_t barrier_offset() {
+        return (table_offset<R_>() + sizeof(int) * (RW + RH) + 7) & ~(size_t)7;
+    }
+    // plane buffers, ring tables, 2 x kHandSlots mbarriers and an abort flag
     template <typename R_> static constexpr size_t smem_bytes() {
-        return sizeof(R_) * ((size_t)kPhiSlots * R + (size_t)kRutSlots * kRut * F + (size_t)kDuSlots * 3 * F) +
-               sizeof(int) * (RW + RH);
+        return barrier_offset<R_>() + 8 * (2 * kHandSlots + 1);
     }
 };
 
@@ -335,30 +370,62 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restr
     for (int i = tid; i < Sh::RW; i += NT) st.ring_a[i] = wrapi(a0 + i - 2, G.na);
     for (int i = tid; i < Sh::RH; i += NT) st.ring_b[i] = wrapi(b0 + i - Sh::RB, G.nb) * G.na;
 
-    const bool producer = tid >= NC;
-    // consumer node and its +-1 offsets along a and b
-    const int ta = tid % TX, tb = tid / TX;
-    const int ga = a0 + ta, gb = b0 + tb;
-    const bool owns = !producer && ga < G.na && gb < G.nb;
-    const int n_ab = gb * G.na + ga;
-    const int dA_m = ga == 0 ? G.na - 1 : -1, dA_p = ga == G.na - 1 ? 1 - G.na : 1;
-    const int dB_m = (gb == 0 ? G.nb - 1 : -1) * G.na, dB_p = (gb == G.nb - 1 ? 1 - G.nb : 1) * G.na;
+    // hand-off ring: full[s] completes when the producers finish iteration u
+    // (u = i - zb + 2, s = u mod D); empty[s] when every consumer has finished
+    // plane c (u = c - zb).  The k-th use of a slot completes its phase k, so
+    // the wait parity is (u / D) & 1; neither side gets two phases ahead of
+    // the other's wait (producers run at most 2 iterations ahead of the plane
+    // they need released, consumers cannot pass the producers).
+    constexpr int D = Sh::kHandSlots;
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(smem_raw + Sh::template barrier_offset<R>());
+    unsigned long long* empty = full + D;
+    volatile int* aborted = reinterpret_cast<volatile int*>(empty + D);
+    if (tid == 0) {
+        *aborted = 0;
+        for (int s = 0; s < D; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, NC);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
+    auto wait = [&](unsigned long long* b, int u) {
+        if (*aborted) return;
+        if (!mbar_wait(b + (u % D), (unsigned)(u / D) & 1u)) {
+            *aborted = 1;
+            atomicAdd(&cnt->timeouts, 1ull);
+        }
+    };
 
-    for (int i = zb - 2; i < ze + 3; ++i) {
-        if (producer) {
-            const int t = tid - NC;
+    if (tid >= NC) {
+        // producers: iteration i builds M(i) and F(i-1).  M(i) and F(i-1)
+        // overwrite the buffers that C(i-4) read last.
+        const int t = tid - NC;
+        for (int i = zb - 2; i < ze + 3; ++i) {
+            const int cw = i - 4;
+            if (cw >= zb && cw < ze) wait(empty, cw - zb);
             const bool m_need = i <= ze + 1 && (walls ? (i >= 0 && i < G.nm) : true);
             if (m_need) st.m_stage(i, t, NP);
             asm volatile("bar.sync 1, %0;" ::"r"(NP));
             const int f = i - 1;
             const bool f_need = f >= zb - 1 && f <= ze && (walls ? (f >= 0 && f < G.nm) : true);
             if (f_need) st.f_stage(f, t, NP);
-        } else {
-            const int c = i - 3;
-            if (c >= zb && c < ze && owns) st.c_stage(c, ta, tb, n_ab, dA_m, dA_p, dB_m, dB_p, cnt);
+            asm volatile("bar.sync 1, %0;" ::"r"(NP));
+            if (t == 0) mbar_arrive(full + ((i - zb + 2) % D));
         }
-        __syncthreads();
+    } else {
+        // consumers: C(c) needs M(c+2) and F(c+1), i.e. producer iteration c+2
+        const int ta = tid % TX, tb = tid / TX;
+        const int ga = a0 + ta, gb = b0 + tb;
+        const bool owns = ga < G.na && gb < G.nb;
+        const int n_ab = gb * G.na + ga;
+        const int dA_m = ga == 0 ? G.na - 1 : -1, dA_p = ga == G.na - 1 ? 1 - G.na : 1;
+        const int dB_m = (gb == 0 ? G.nb - 1 : -1) * G.na, dB_p = (gb == G.nb - 1 ? 1 - G.nb : 1) * G.na;
+        for (int c = zb; c < ze; ++c) {
+            wait(full, c - zb + 4);
+            if (owns) st.c_stage(c, ta, tb, n_ab, dA_m, dA_p, dB_m, dB_p, cnt);
+            mbar_arrive(empty + ((c - zb) % D));
+        }
     }
 }
 

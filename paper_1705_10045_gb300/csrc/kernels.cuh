@@ -25,6 +25,7 @@ struct Counters {
     unsigned long long clamps;
     unsigned long long bad;
     unsigned long long unstable;
+    unsigned long long timeouts;   // fused step: a hand-off wait gave up (never expected)
 };
 
 template <typename R> __device__ __forceinline__ bool finite_pos(R v) { return v > R(0) && isfinite(v); }

@@ -101,6 +101,11 @@ int sync_and_latch(lbm_handle* h) {
     if (rc) return rc;
     rc = cuda_error(cudaStreamSynchronize(h->stream), "stream synchronize");
     if (rc) return rc;
+    if (c.timeouts) {
+        set_error("fused step: a producer/consumer hand-off wait gave up (" + std::to_string(c.timeouts) +
+                  " times); the results of the steps since the last check are not valid");
+        return LBM_ERR_CUDA;
+    }
     if (c.bad > h->reported_bad) {
         h->reported_bad = c.bad;
         set_error("non-physical state: non-finite or non-positive density or energy at " + std::to_string(c.bad) +

@@ -257,15 +257,17 @@ constexpr int kReduceBlocks = 1024;
 constexpr int kReduceThreads = 256;
 constexpr int kSums = 5;   // mass, momentum x, y, z, energy
 
-struct Kahan {
-    double s = 0.0, c = 0.0;
-    __device__ void add(double v) {
-        double y = v - c;
-        double t = s + y;
+// compensated (Kahan) summation in type T; the sum is s - c
+template <typename T> struct KahanT {
+    T s = T(0), c = T(0);
+    __device__ void add(T v) {
+        T y = v - c;
+        T t = s + y;
         c = (t - s) - y;
         s = t;
     }
 };
+using Kahan = KahanT<double>;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -276,22 +278,27 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int Q, typename S, typename R>
 __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const S* __restrict__ pop, KParams<R> p,
                                                                 double* __restrict__ partials) {
-    Kahan acc[kSums];
+    // Each thread sums its nodes (about nn / 262144 of them) with compensation
+    // in the arithmetic type: the node moments are of that type already, and
+    // compensated FP32 keeps a partial to about one rounding of its value,
+    // while FP64 arithmetic runs at a small fraction of the FP32 rate on this
+    // GPU.  The partials are combined in FP64 from here on.
+    KahanT<R> acc[kSums];
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.nn; i += stride) {
         R rho, jx, jy, jz, E;
         node_moments<Q, S, R>(pop, p.nn, i, p, rho, jx, jy, jz, E);
-        acc[0].add((double)rho);
-        acc[1].add((double)jx);
-        acc[2].add((double)jy);
-        acc[3].add((double)jz);
-        acc[4].add((double)E);
+        acc[0].add(rho);
+        acc[1].add(jx);
+        acc[2].add(jy);
+        acc[3].add(jz);
+        acc[4].add(E);
     }
     __shared__ double sh[kSums][kReduceThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < kSums; ++q) {
-        double v = warp_sum(acc[q].s - acc[q].c);
+        double v = warp_sum((double)acc[q].s - (double)acc[q].c);
         if (lane == 0) sh[q][warp] = v;
     }
     __syncthreads();

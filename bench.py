@@ -94,6 +94,22 @@ def _measured_traffic_per_node():
         return None, None
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's);
+    x itself when there is no process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Lattice updates of all ranks (one replica each) per second, in millions."""
+    return nodes_per_rank * steps * world / seconds / 1e6
+
+
 def _peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -414,9 +430,7 @@ def main():
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist)
         dist.barrier()
     diag = sim.diagnostics()
 
@@ -434,9 +448,7 @@ def main():
     lbm.lbm_moments(sim.h, out["rho"], out["u"], out["T"], out["P"])
     e2e_s = time.perf_counter() - t0
     if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist)
     h2d = (rho_h.numel() + u_h.numel() + eps_h.numel()) * 8
     d2h = sum(v.numel() for v in out.values()) * 8
     sim.close()
@@ -455,7 +467,7 @@ def main():
         algo_bytes = {"collide_kernel": 4 * 19 * 4 + 8 * 4}.get(top, 4 * 19 * 4)
         achieved = algo_bytes * nn / (prof[top] * 1e-3) / 1e9
         traffic_per_node, traffic_src = _measured_traffic_per_node() if top == "fused_step_kernel" else (None, None)
-        value = nn * args.steps * ws / (ms * 1e-3) / 1e6
+        value = whole_job_mlups(nn, args.steps, ws, ms * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -469,7 +481,7 @@ def main():
                          "algorithmic_bytes_per_node": algo_bytes, "kernel_ms": prof,
                          "step_bytes_per_node": 4 * 19 * 4,
                          "step_frac": 4 * 19 * 4 * nn / (ms / args.steps * 1e-3) / 1e9 / peak},
-            "e2e": {"value": nn * args.steps * ws / e2e_s / 1e6, "unit": "MLUPS",
+            "e2e": {"value": whole_job_mlups(nn, args.steps, ws, e2e_s), "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
             "gpu_launches": launches * args.steps,
             "clocks": clk.summary(),

@@ -51,6 +51,10 @@ extern "C" {
 #define LBM_ERR_INVALID_ARG (-1)
 #define LBM_ERR_UNSTABLE_PARAMS (-2)
 #define LBM_ERR_OOM (-3)
+/* A CUDA call failed, or a wait inside the fused step gave up (the producer
+ * and consumer warps of a CTA hand planes over through shared-memory
+ * barriers whose waits are bounded to about half a second); the state of the
+ * steps since the last synchronising call is then not valid. */
 #define LBM_ERR_CUDA (-4)
 #define LBM_ERR_NONPHYSICAL (-5)
 

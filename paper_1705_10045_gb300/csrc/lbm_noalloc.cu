@@ -3,9 +3,10 @@
 // Some callers cannot allocate device memory: programs whose device memory is
 // owned by another framework's pool (every byte must come from that pool), and
 // loops that must not let an allocation synchronise the device and stall
-// their other streams.  For them this entry point computes the same FP64
-// Kahan sums as lbm_diagnostics on a population buffer they own, using only
-// a fixed scratch array that is part of the loaded library image.
+// their other streams.  For them this entry point computes the same
+// compensated sums as lbm_diagnostics (per-thread partials, combined in FP64)
+// on a population buffer they own, using only a fixed scratch array that is
+// part of the loaded library image.
 //
 // The scratch is a file-scope __device__ array: every GPU that loads the
 // library holds it (40,960 bytes) until the process exits.  Its name in host

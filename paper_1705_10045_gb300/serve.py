@@ -11,6 +11,16 @@ memory is freed for the next arrivals.  Admission is first come, first
 served: a job that does not fit blocks later arrivals (no reordering), so
 large jobs are not starved.
 
+Which resident jobs advance in a round is the policy's choice:
+
+* ``"fill"`` (default): jobs in admission order, the oldest first, are
+  advanced while their node count adds up to at most the larger of
+  ``fill_nodes`` (enough nodes to keep the GPU busy) and (1 + ``ride``) times
+  the oldest job's; the others wait with their state resident.  Large jobs
+  then run nearly one at a time in arrival order, and small jobs ride along
+  at almost no cost, which keeps the latency of both low.
+* ``"all"``: every resident job advances every round (processor sharing).
+
 Latency of a job is completion (results on the host) minus arrival;
 throughput is completed jobs per wall-clock second.  ``run_sequential`` runs
 the same trace the plain way (one job at a time, lbm_step per job) for
@@ -79,7 +89,8 @@ class Server:
     """Continuous batching of jobs of one lattice and storage format."""
 
     def __init__(self, lattice: int, storage: int, memory_budget: Optional[int] = None, max_slots: int = 4096,
-                 quantum: int = 128, device: int = 0, keep_fields: bool = True):
+                 quantum: int = 128, device: int = 0, keep_fields: bool = True, policy: str = "fill",
+                 fill_nodes: int = 8_000_000, ride: float = 0.25):
         import torch
         self.lattice, self.storage = lattice, storage
         if memory_budget is None:
@@ -89,6 +100,9 @@ class Server:
         self.max_slots = max_slots
         self.quantum = int(quantum)
         self.keep_fields = keep_fields
+        if policy not in ("fill", "all"):
+            raise ValueError(f"unknown policy {policy}")
+        self.policy, self.fill_nodes, self.ride = policy, int(fill_nodes), float(ride)
         self.batch = lbm.LbmBatch(lattice=lattice, storage=storage, device=device)
         self.resident = {}          # slot id -> (job, bytes)
         self.bytes_in_use = 0
@@ -146,15 +160,36 @@ class Server:
                 if wait > 0:
                     time.sleep(wait)
                 continue
-            # advance every resident job by the quantum (each stops at its own budget);
+            # advance the chosen jobs by the quantum (each stops at its own budget);
             # a shorter quantum when a job is about to finish keeps its latency low
-            left = [self.batch.status(s)[1] for s in self.resident]
+            active = self._choose()
+            left = [self.batch.status(s)[1] for s in active]
             q = max(1, min(self.quantum, min(left)))
-            lu += sum(min(q, l) * _nodes(self.resident[s][0].params) for s, l in zip(list(self.resident), left))
+            paused = [(s, self.batch.status(s)[1]) for s in self.resident if s not in active]
+            for s, _ in paused:
+                self.batch.set_budget(s, 0)
+            lu += sum(min(q, l) * _nodes(self.resident[s][0].params) for s, l in zip(active, left))
             self.batch.step(q)
-            for s in [s for s in list(self.resident) if self.batch.status(s)[1] == 0]:
+            for s, l in paused:
+                self.batch.set_budget(s, l)
+            for s in [s for s in active if self.batch.status(s)[1] == 0]:
                 self._retire(s, now)
         return _stats(queue, now(), max_resident, peak, lu)
+
+    def _choose(self) -> list:
+        """Resident slots that advance this round (admission order)."""
+        order = list(self.resident)
+        if self.policy == "all":
+            return order
+        head = _nodes(self.resident[order[0]][0].params)
+        target = max(self.fill_nodes, (1.0 + self.ride) * head)
+        active, total = [], 0
+        for s in order:
+            n = _nodes(self.resident[s][0].params)
+            if not active or total + n <= target:
+                active.append(s)
+                total += n
+        return active
 
     def close(self):
         self.batch.close()

@@ -27,9 +27,12 @@ def _alone(job):
         sim.close()
 
 
-def test_served_results_equal_jobs_run_alone():
+@pytest.mark.parametrize("policy", [dict(policy="all"), dict(policy="fill", fill_nodes=0, ride=0.25)])
+def test_served_results_equal_jobs_run_alone(policy):
+    # fill_nodes = 0 makes the fill policy pause every job much larger than
+    # the oldest, so jobs stop and resume between rounds
     jobs = _small_trace()
-    srv = serve.Server(lbm.LBM_D3Q19, lbm.LBM_STORE_FP32, quantum=32)
+    srv = serve.Server(lbm.LBM_D3Q19, lbm.LBM_STORE_FP32, quantum=32, **policy)
     try:
         st = srv.run(jobs)
     finally:

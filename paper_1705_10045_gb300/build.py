@@ -22,10 +22,12 @@ LIB = os.path.join(BUILD, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # --fmad=false: every floating-point operation is rounded on its own, in source
 # order, so results do not depend on which kernel or CTA shape computed them
-# (a domain in a batch evolves bit for bit as it does alone); it costs about
-# 1 % of the fused step's time.
+# (a domain in a batch evolves bit for bit as it does alone); the hot
+# arithmetic spells out its fused multiply-adds, which the flag leaves alone.
+# -prec-div=false -prec-sqrt=false: FP32 division and square root by the
+# hardware's approximate instructions (within 2 ulp); FP64 is unaffected.
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "--fmad=false",
-         "-Xptxas", "-warn-spills"]
+         "-prec-div=false", "-prec-sqrt=false", "-Xptxas", "-warn-spills"]
 
 
 def _nvcc() -> str:

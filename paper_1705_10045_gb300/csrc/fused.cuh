@@ -272,16 +272,20 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         if (P - rho * third >= R(0)) atomicAdd(&cnt->clamps, 1ull);
 
         const int n = c * plane_n + n_ab;
+        // the node's population k sits at qn + k nn (N) and qn + (Q + k) nn (g);
+        // the pointers walk from one population to the next
+        const S* qn = src + n;
+        const S* qg = qn + (size_t)Q * nn;
         R hv[Q];
         R E = 0;
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            hv[k] = Store<S, R>::load(src, (size_t)(Q + k) * nn + n, R(V::w(k)) * p->E_ref);
+            hv[k] = Store<S, R>::load(qg, 0, R(V::w(k)) * p->E_ref);
             E += hv[k];
+            qg += nn;
         }
         if (!(finite_pos(rho) && finite_pos(E))) atomicAdd(&cnt->bad, 1ull);
         const R dEoverE = dE / E;
-
         // node offsets of x + c_k: +-1 along a and b (periodic), along the
         // march axis periodic or bounced at a wall
         const int dM_m = (c == 0 ? nm - 1 : -1) * plane_n, dM_p = (c == nm - 1 ? 1 - nm : 1) * plane_n;
@@ -292,36 +296,45 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         //   g*_k = (1 - omega_E + dE/E) g_k + E (omega_E e0_k + [pseudoforce] de_k)
         // with e0 = N^eq(rho,u)/rho and de = (N^eq(rho,u+du) - N^eq(rho,u))/rho.
         // For opposite directions k, k+1 (c -> -c) both split into an even
-        // part (shared) and an odd part (sign flip).
-        const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        const R dsq = dv[0] * (R(2) * u[0] + dv[0]) + dv[1] * (R(2) * u[1] + dv[1]) +
-                      dv[2] * (R(2) * u[2] + dv[2]);
-        const R base0 = R(1) - R(1.5) * usq, dbase = R(-1.5) * dsq;
+        // part (shared) and an odd part (sign flip).  Products that feed a sum
+        // are written as explicit fused multiply-adds, so every kernel that
+        // runs this code rounds them the same way.
+        const R usq = fma(u[0], u[0], fma(u[1], u[1], u[2] * u[2]));
+        const R dsq = fma(dv[0], fma(R(2), u[0], dv[0]), fma(dv[1], fma(R(2), u[1], dv[1]), dv[2] * fma(R(2), u[2], dv[2])));
+        const R base0 = fma(R(-1.5), usq, R(1)), dbase = R(-1.5) * dsq;
         const R om = p->omega, omE = p->omega_E;
         const R fN = R(1) - om, fG = R(1) - omE + dEoverE;
-        const R pf = p->pseudoforce ? R(1) : R(0);
-
+        const R rho_om = rho * om, E_omE = E * omE, E_pf = p->pseudoforce ? E : R(0);
         const unsigned nbits = Store<S, R>::kStochastic ? node_bits(step, (unsigned)n) : 0u;
+        S* dn = dst + n;                    // population k of the node's slot, N set
+        S* dg = dn + (size_t)Q * nn;        // and g set
         auto emit = [&](int k, R e0, R de, R fv, R hvk) {
-            const R fo = fv * fN + rho * (om * e0 + de);
-            const R ho = hvk * fG + E * (omE * e0 + pf * de);
+            const R fo = fma(fv, fN, fma(rho_om, e0, rho * de));
+            const R ho = fma(hvk, fG, fma(E_omE, e0, E_pf * de));
             // push to x + c_k, or bounce back at a wall on the march axis
             const bool bounce = (M::m(k) == -1 && wall_lo) || (M::m(k) == 1 && wall_hi);
-            const int ko = bounce ? opposite(k) : k;
-            int to = n;
-            if (!bounce) {
-                if (M::a(k) == 1) to += dA_p; else if (M::a(k) == -1) to += dA_m;
-                if (M::b(k) == 1) to += dB_p; else if (M::b(k) == -1) to += dB_m;
-                if (M::m(k) == 1) to += dM_p; else if (M::m(k) == -1) to += dM_m;
-            }
+            int to = 0;
+            if (M::a(k) == 1) to += dA_p; else if (M::a(k) == -1) to += dA_m;
+            if (M::b(k) == 1) to += dB_p; else if (M::b(k) == -1) to += dB_m;
+            if (M::m(k) == 1) to += dM_p; else if (M::m(k) == -1) to += dM_m;
             // opposite directions share a weight, so the FP16 shift of slot ko is w_k ref
             const R wk = R(V::w(k));
-            Store<S, R>::store(dst, (size_t)ko * nn + to, fo, wk * p->rho_ref, slot_bits(nbits, k));
-            Store<S, R>::store(dst, (size_t)(Q + ko) * nn + to, ho, wk * p->E_ref, slot_bits(nbits, Q + k));
+            const unsigned rN = slot_bits(nbits, k), rG = slot_bits(nbits, Q + k);
+            if (bounce) {
+                const long long back = (long long)(opposite(k) - k) * (long long)nn;
+                Store<S, R>::store(dn + back, 0, fo, wk * p->rho_ref, rN);
+                Store<S, R>::store(dg + back, 0, ho, wk * p->E_ref, rG);
+            } else {
+                Store<S, R>::store(dn + to, 0, fo, wk * p->rho_ref, rN);
+                Store<S, R>::store(dg + to, 0, ho, wk * p->E_ref, rG);
+            }
+            dn += nn;
+            dg += nn;
         };
         {
             const R w0 = R(V::w(0));
-            emit(0, w0 * base0, w0 * dbase, Store<S, R>::load(src, n, w0 * p->rho_ref), hv[0]);
+            emit(0, w0 * base0, w0 * dbase, Store<S, R>::load(qn, 0, w0 * p->rho_ref), hv[0]);
+            qn += nn;
         }
 #pragma unroll
         for (int k = 1; k < Q; k += 2) {
@@ -330,10 +343,11 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
             if (M::a(k) == 1) { cu += u[0]; cd += dv[0]; } else if (M::a(k) == -1) { cu -= u[0]; cd -= dv[0]; }
             if (M::b(k) == 1) { cu += u[1]; cd += dv[1]; } else if (M::b(k) == -1) { cu -= u[1]; cd -= dv[1]; }
             if (M::m(k) == 1) { cu += u[2]; cd += dv[2]; } else if (M::m(k) == -1) { cu -= u[2]; cd -= dv[2]; }
-            const R ev = wk * (base0 + R(4.5) * cu * cu), od = wk * (R(3) * cu);
-            const R dv_e = wk * (R(4.5) * cd * (R(2) * cu + cd) + dbase), dv_o = wk * (R(3) * cd);
-            const R fa = Store<S, R>::load(src, (size_t)k * nn + n, wk * p->rho_ref);
-            const R fb = Store<S, R>::load(src, (size_t)(k + 1) * nn + n, wk * p->rho_ref);
+            const R ev = wk * fma(R(4.5) * cu, cu, base0), od = (R(3) * wk) * cu;
+            const R dv_e = wk * fma(R(4.5) * cd, fma(R(2), cu, cd), dbase), dv_o = (R(3) * wk) * cd;
+            const R fa = Store<S, R>::load(qn, 0, wk * p->rho_ref);
+            const R fb = Store<S, R>::load(qn + nn, 0, wk * p->rho_ref);
+            qn += 2 * nn;
             emit(k, ev + od, dv_e + dv_o, fa, hv[k]);
             emit(k + 1, ev - od, dv_e - dv_o, fb, hv[k + 1]);
         }

@@ -35,6 +35,8 @@
 // (c_{k+1} = -c_k), which share the even part of every term.
 #pragma once
 
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace lbm {
@@ -308,49 +310,56 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         const unsigned nbits = Store<S, R>::kStochastic ? node_bits(step, (unsigned)n) : 0u;
         S* dn = dst + n;                    // population k of the node's slot, N set
         S* dg = dn + (size_t)Q * nn;        // and g set
-        auto emit = [&](int k, R e0, R de, R fv, R hvk) {
-            const R fo = fma(fv, fN, fma(rho_om, e0, rho * de));
-            const R ho = fma(hvk, fG, fma(E_omE, e0, E_pf * de));
-            // push to x + c_k, or bounce back at a wall on the march axis
-            const bool bounce = (M::m(k) == -1 && wall_lo) || (M::m(k) == 1 && wall_hi);
-            int to = 0;
-            if (M::a(k) == 1) to += dA_p; else if (M::a(k) == -1) to += dA_m;
-            if (M::b(k) == 1) to += dB_p; else if (M::b(k) == -1) to += dB_m;
-            if (M::m(k) == 1) to += dM_p; else if (M::m(k) == -1) to += dM_m;
-            // opposite directions share a weight, so the FP16 shift of slot ko is w_k ref
-            const R wk = R(V::w(k));
-            const unsigned rN = slot_bits(nbits, k), rG = slot_bits(nbits, Q + k);
-            if (bounce) {
-                const long long back = (long long)(opposite(k) - k) * (long long)nn;
-                Store<S, R>::store(dn + back, 0, fo, wk * p->rho_ref, rN);
-                Store<S, R>::store(dg + back, 0, ho, wk * p->E_ref, rG);
-            } else {
-                Store<S, R>::store(dn + to, 0, fo, wk * p->rho_ref, rN);
-                Store<S, R>::store(dg + to, 0, ho, wk * p->E_ref, rG);
+        // the collision and push, instantiated once for planes next to a wall
+        // (WALL: some directions bounce back) and once for all other planes
+        auto collide = [&](auto wall_tag) {
+            constexpr bool WALL = decltype(wall_tag)::value;
+            auto emit = [&](int k, R e0, R de, R fv, R hvk) {
+                const R fo = fma(fv, fN, fma(rho_om, e0, rho * de));
+                const R ho = fma(hvk, fG, fma(E_omE, e0, E_pf * de));
+                // push to x + c_k, or bounce back at a wall on the march axis
+                const bool bounce = WALL && ((M::m(k) == -1 && wall_lo) || (M::m(k) == 1 && wall_hi));
+                int to = 0;
+                if (M::a(k) == 1) to += dA_p; else if (M::a(k) == -1) to += dA_m;
+                if (M::b(k) == 1) to += dB_p; else if (M::b(k) == -1) to += dB_m;
+                if (M::m(k) == 1) to += dM_p; else if (M::m(k) == -1) to += dM_m;
+                // opposite directions share a weight, so the FP16 shift of slot ko is w_k ref
+                const R wk = R(V::w(k));
+                const unsigned rN = slot_bits(nbits, k), rG = slot_bits(nbits, Q + k);
+                if (bounce) {
+                    const long long back = (long long)(opposite(k) - k) * (long long)nn;
+                    Store<S, R>::store(dn + back, 0, fo, wk * p->rho_ref, rN);
+                    Store<S, R>::store(dg + back, 0, ho, wk * p->E_ref, rG);
+                } else {
+                    Store<S, R>::store(dn + to, 0, fo, wk * p->rho_ref, rN);
+                    Store<S, R>::store(dg + to, 0, ho, wk * p->E_ref, rG);
+                }
+                dn += nn;
+                dg += nn;
+            };
+            {
+                const R w0 = R(V::w(0));
+                emit(0, w0 * base0, w0 * dbase, Store<S, R>::load(qn, 0, w0 * p->rho_ref), hv[0]);
+                qn += nn;
             }
-            dn += nn;
-            dg += nn;
-        };
-        {
-            const R w0 = R(V::w(0));
-            emit(0, w0 * base0, w0 * dbase, Store<S, R>::load(qn, 0, w0 * p->rho_ref), hv[0]);
-            qn += nn;
-        }
 #pragma unroll
-        for (int k = 1; k < Q; k += 2) {
-            const R wk = R(V::w(k));
-            R cu = 0, cd = 0;
-            if (M::a(k) == 1) { cu += u[0]; cd += dv[0]; } else if (M::a(k) == -1) { cu -= u[0]; cd -= dv[0]; }
-            if (M::b(k) == 1) { cu += u[1]; cd += dv[1]; } else if (M::b(k) == -1) { cu -= u[1]; cd -= dv[1]; }
-            if (M::m(k) == 1) { cu += u[2]; cd += dv[2]; } else if (M::m(k) == -1) { cu -= u[2]; cd -= dv[2]; }
-            const R ev = wk * fma(R(4.5) * cu, cu, base0), od = (R(3) * wk) * cu;
-            const R dv_e = wk * fma(R(4.5) * cd, fma(R(2), cu, cd), dbase), dv_o = (R(3) * wk) * cd;
-            const R fa = Store<S, R>::load(qn, 0, wk * p->rho_ref);
-            const R fb = Store<S, R>::load(qn + nn, 0, wk * p->rho_ref);
-            qn += 2 * nn;
-            emit(k, ev + od, dv_e + dv_o, fa, hv[k]);
-            emit(k + 1, ev - od, dv_e - dv_o, fb, hv[k + 1]);
-        }
+            for (int k = 1; k < Q; k += 2) {
+                const R wk = R(V::w(k));
+                R cu = 0, cd = 0;
+                if (M::a(k) == 1) { cu += u[0]; cd += dv[0]; } else if (M::a(k) == -1) { cu -= u[0]; cd -= dv[0]; }
+                if (M::b(k) == 1) { cu += u[1]; cd += dv[1]; } else if (M::b(k) == -1) { cu -= u[1]; cd -= dv[1]; }
+                if (M::m(k) == 1) { cu += u[2]; cd += dv[2]; } else if (M::m(k) == -1) { cu -= u[2]; cd -= dv[2]; }
+                const R ev = wk * fma(R(4.5) * cu, cu, base0), od = (R(3) * wk) * cu;
+                const R dv_e = wk * fma(R(4.5) * cd, fma(R(2), cu, cd), dbase), dv_o = (R(3) * wk) * cd;
+                const R fa = Store<S, R>::load(qn, 0, wk * p->rho_ref);
+                const R fb = Store<S, R>::load(qn + nn, 0, wk * p->rho_ref);
+                qn += 2 * nn;
+                emit(k, ev + od, dv_e + dv_o, fa, hv[k]);
+                emit(k + 1, ev - od, dv_e - dv_o, fb, hv[k + 1]);
+            }
+        };
+        if (wall_lo || wall_hi) collide(std::true_type{});
+        else collide(std::false_type{});
     }
 };
 

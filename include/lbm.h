@@ -202,7 +202,9 @@ void lbm_destroy(lbm_handle* h);
  * of its per-step update for many simulation jobs. */
 typedef struct lbm_batch lbm_batch;
 
-/* Device memory in bytes a domain with parameters *p needs (admission control). */
+/* Device memory in bytes a domain with parameters *p needs (admission control),
+ * counting the staging planes it keeps once fields have moved between it and
+ * host memory (lbm_init or lbm_moments with host pointers). */
 size_t lbm_domain_bytes(const lbm_params* p);
 
 /* New empty batch for common->lattice and common->storage on common->device.

@@ -140,10 +140,14 @@ size_t lbm_domain_bytes(const lbm_params* p) {
     const size_t elem = p->storage == LBM_STORE_FP64 ? 8 : (p->storage == LBM_STORE_FP32 ? 4 : 2);
     const size_t fields = p->lattice == LBM_D2Q9 ? lbm::Backend<9>::field_bytes(p->storage)
                                                  : lbm::Backend<19>::field_bytes(p->storage);
-    // two population buffers of 2Q planes, the moments fields, reduction and counter scratch
+    // two population buffers of 2Q planes, the moments fields, reduction and counter scratch,
+    // the staging planes a domain keeps once it has been initialised from host fields
+    // (rho, eps and d velocity planes, plus one), and the coexistence table
+    const size_t d = p->lattice == LBM_D2Q9 ? 2 : 3;
+    const size_t staging = sizeof(double) * (d + 3) * nn;
     const size_t coex = p->latent != 0.0 ? 2 * (size_t)(lbm::kCoexIntervals + 1) * (elem == 8 ? 8 : 4) : 0;
     return 2 * 2 * (size_t)p->lattice * nn * elem + fields * nn +
-           sizeof(double) * (lbm::kSums * lbm::kReduceBlocks + 8) + sizeof(lbm::Counters) + coex;
+           sizeof(double) * (lbm::kSums * lbm::kReduceBlocks + 8) + sizeof(lbm::Counters) + staging + coex;
 }
 
 int lbm_batch_create(const lbm_params* common, lbm_batch** out) {

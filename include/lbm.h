@@ -255,6 +255,90 @@ int lbm_batch_sync(lbm_batch* b);
 /* Destroy every domain and the batch.  NULL is allowed. */
 void lbm_batch_destroy(lbm_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Slabs: one domain cut along its last axis (y for D2Q9, z for D3Q19) into
+ * `count` sub-domains that step independently and swap halo planes after
+ * every step.  This is the decomposition a run over several GPUs needs (one
+ * slab per GPU, the halo swap over the interconnect); within one process the
+ * slabs live on one device and the swap is a device-to-device copy.  The
+ * paper gives no parallel scheme; the halo depth follows from the reach of
+ * one step along an axis: the collision of plane c reads the moments and the
+ * velocity change du (Sec. 3, force with the stencil of Sec. 3, Eq. (edm))
+ * of planes c-1..c+1, du reads Phi one plane further, and the finite
+ * differences of Sec. 4 read planes c-1..c+1; so plane c after a step depends
+ * on planes c-2..c+2 before it, and with LBM_SLAB_HALO = 3 halo planes beyond
+ * each cut every plane a slab owns is computed exactly.  The slab's own
+ * boundary treatment beyond its outer halo plane (a wrap, or a wall that the
+ * whole domain does not have there) reaches only its two outermost halo
+ * planes, which the swap overwrites.  FP64 and FP32 slabs reproduce the
+ * undivided domain bit for bit; FP16 slabs key their stochastic rounding by
+ * node index within the slab, so they agree in distribution, not in bits. */
+#define LBM_SLAB_HALO 3
+
+typedef struct lbm_slab {
+    int first;       /* first plane the slab owns, as an index of the whole domain's last axis */
+    int own;         /* planes it owns: nm / count, plus one for the first nm % count slabs */
+    int lo, hi;      /* halo planes below / above the owned ones: LBM_SLAB_HALO at a cut, 0 at a wall */
+    int below, above;/* slab across the lower / upper cut (periodic domains wrap), -1 at a wall */
+    lbm_params p;    /* the slab's own domain: last axis lo + own + hi planes; a fixed wall
+                        temperature is kept only where the slab ends at the domain's wall */
+} lbm_slab;
+
+/* Host-only plan of slab i of `count` for the domain *p (no device needed).
+ * Errors (LBM_ERR_INVALID_ARG): null pointers, unknown lattice, count < 1,
+ * i outside [0, count), or slabs that would own fewer than LBM_SLAB_HALO
+ * planes. */
+int lbm_slab_plan(const lbm_params* p, int count, int i, lbm_slab* out);
+
+typedef struct lbm_slabs lbm_slabs;
+
+/* The domain *p as `count` slabs on p->device, all enqueued on p->stream
+ * (count = 1 is the undivided domain).  The library owns the slab handles
+ * and a field buffer of (d + 3) planes of doubles per node of the largest
+ * slab.  Errors as lbm_slab_plan and lbm_create. */
+int lbm_slabs_create(const lbm_params* p, int count, lbm_slabs** out);
+int lbm_slabs_count(const lbm_slabs* s);
+
+/* Handle of slab i (owned by the slabs object; NULL if out of range). */
+lbm_handle* lbm_slabs_domain(lbm_slabs* s, int i);
+
+/* As lbm_init for the whole domain's fields (same layout and checks); each
+ * slab is initialised from its own and its halo planes.  Synchronising. */
+int lbm_slabs_init(lbm_slabs* s, const double* rho, const double* u, const double* eps, int mem);
+
+/* n steps: every slab steps once, then every halo is refreshed from the
+ * neighbours' owned planes, n times (asynchronous on p->stream). */
+int lbm_slabs_step(lbm_slabs* s, int n);
+
+/* As lbm_moments for the whole domain, assembled from the slabs' owned
+ * planes.  Synchronising; LBM_ERR_NONPHYSICAL as lbm_moments. */
+int lbm_slabs_moments(lbm_slabs* s, double* rho, double* u, double* T, double* P, int mem);
+
+/* As lbm_diagnostics for the whole domain: the sums over each slab's owned
+ * planes (per-thread compensated, FP64 across threads and then across slabs
+ * in slab order); out[5], out[6] add up the slabs' counters, halo planes
+ * included; out[7] the steps since lbm_slabs_init.  Synchronising. */
+int lbm_slabs_diagnostics(lbm_slabs* s, double out[8]);
+
+/* Wait for every slab; returns a latched device error if any. */
+int lbm_slabs_sync(lbm_slabs* s);
+void lbm_slabs_destroy(lbm_slabs* s);
+
+/* Halo exchange between processes (one slab handle per process): bytes of one
+ * plane of the last axis over all 2Q population arrays in the handle's
+ * storage format. */
+size_t lbm_plane_bytes(const lbm_handle* h);
+
+/* Copy planes [first, first + count) of the current populations out of / into
+ * buf, laid out as 2Q rows (N_0..N_{Q-1}, g_0..g_{Q-1}) of count planes each,
+ * storage format.  mem = LBM_MEM_DEVICE: one kernel on the handle's stream,
+ * asynchronous (the caller orders its own use of buf on that stream or
+ * synchronises); LBM_MEM_HOST: synchronising.  Errors (LBM_ERR_INVALID_ARG):
+ * null pointers, bad mem flag, no state yet, planes outside the handle's
+ * last axis. */
+int lbm_get_planes(lbm_handle* h, int first, int count, void* buf, int mem);
+int lbm_set_planes(lbm_handle* h, int first, int count, const void* buf, int mem);
+
 /* The paper has no counterpart to this call: it is library plumbing for
  * callers that cannot allocate device memory, either because all their
  * device memory belongs to another framework's pool or because an allocation

@@ -1,0 +1,527 @@
+// Slabs: one domain cut along its last axis (y for D2Q9, z for D3Q19) into
+// sub-domains that each step on their own and swap halo planes after every
+// step (lbm_slab_plan, lbm_slabs_*, lbm_plane_bytes, lbm_get_planes,
+// lbm_set_planes).
+//
+// Reach of one step along the last axis.  The collision of plane c needs the
+// moments of planes c-1..c+1 (the finite differences of Sec. 4 and Sec. 6.2)
+// and the velocity change du of planes c-1..c+1 (u* = u + du/2 inside
+// div u*), and du of plane c+1 needs Phi of planes c..c+2 (the force of
+// Sec. 3): the post-collision values of plane c depend on the populations of
+// planes c-2..c+2.  Streaming then moves them one plane.  So a slab that
+// holds LBM_SLAB_HALO = 3 copies of its neighbours' planes beyond each cut
+// computes every plane it owns exactly: its halo plane next to the cut
+// depends on planes at most two further out, which it holds, and whatever the
+// slab's own boundary treatment does beyond its last halo plane (a wrap or a
+// wall that is not there in the whole domain) reaches at most the two outer
+// halo planes.  After a step the halo planes are stale; the exchange
+// overwrites all three with the neighbours' new planes, and the slabs need no
+// population-by-population swap across the cut.
+//
+// The cost is 2 x 3 planes recomputed per cut and per step, plus the copies.
+// Every slab uses the same per-node arithmetic as the whole domain, so FP64
+// and FP32 slabs reproduce the undivided domain bit for bit.  FP16 storage
+// keys its stochastic rounding by the node index within a handle, so FP16
+// slabs round differently (same distribution, not the same bits).
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+struct lbm_slabs {
+    lbm_params p;                  // the whole domain
+    int count = 0;
+    int D = 0;
+    long long plane = 0;           // nodes per plane of the last axis
+    long long nn = 0;              // nodes of the whole domain
+    std::vector<lbm_slab> plan;
+    std::vector<lbm_handle*> h;
+    double* tmp = nullptr;         // (D + 3) field planes of the largest slab
+    double* partials = nullptr;    // reduction partials, then kSums results
+    long long steps = 0;
+};
+
+namespace {
+
+using lbm::cuda_error;
+using lbm::set_error;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int last_axis(const lbm_params& p) { return p.lattice == LBM_D2Q9 ? p.ny : p.nz; }
+long long plane_nodes(const lbm_params& p) { return p.lattice == LBM_D2Q9 ? (long long)p.nx : (long long)p.nx * p.ny; }
+
+// rows of `width` bytes at src + r * spitch -> dst + r * dpitch, r < gridDim.y
+template <typename W>
+__global__ void __launch_bounds__(256) copy_rows_kernel(const unsigned char* __restrict__ src, long long spitch,
+                                                        unsigned char* __restrict__ dst, long long dpitch,
+                                                        long long words) {
+    const W* s = reinterpret_cast<const W*>(src + (long long)blockIdx.y * spitch);
+    W* d = reinterpret_cast<W*>(dst + (long long)blockIdx.y * dpitch);
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (long long)gridDim.x * blockDim.x)
+        d[w] = s[w];
+}
+
+// Copy `rows` strided rows in the widest word that divides every address,
+// pitch and width (16, 8, 4 or 2 bytes; population values are at least 2).
+int copy_rows(const void* src, long long spitch, void* dst, long long dpitch, long long width, int rows,
+              cudaStream_t stream) {
+    if (width <= 0 || rows <= 0) return LBM_OK;
+    const unsigned long long all = (unsigned long long)(size_t)src | (unsigned long long)(size_t)dst |
+                                   (unsigned long long)spitch | (unsigned long long)dpitch |
+                                   (unsigned long long)width;
+    const int wb = (all & 15) == 0 ? 16 : (all & 7) == 0 ? 8 : (all & 3) == 0 ? 4 : 2;
+    const long long words = width / wb;
+    long long bx = (words + 255) / 256;
+    if (bx > 1024) bx = 1024;
+    const dim3 grid((unsigned)bx, (unsigned)rows);
+    const auto* s = static_cast<const unsigned char*>(src);
+    auto* d = static_cast<unsigned char*>(dst);
+    switch (wb) {
+        case 16: copy_rows_kernel<uint4><<<grid, 256, 0, stream>>>(s, spitch, d, dpitch, words); break;
+        case 8: copy_rows_kernel<unsigned long long><<<grid, 256, 0, stream>>>(s, spitch, d, dpitch, words); break;
+        case 4: copy_rows_kernel<unsigned><<<grid, 256, 0, stream>>>(s, spitch, d, dpitch, words); break;
+        default: copy_rows_kernel<unsigned short><<<grid, 256, 0, stream>>>(s, spitch, d, dpitch, words); break;
+    }
+    return cuda_error(cudaGetLastError(), "plane copy launch");
+}
+
+// planes [first, first + count) of every population array of the current state
+int copy_planes(lbm_handle* dst, int dst_first, const lbm_handle* src, int src_first, int count) {
+    const long long plane = plane_nodes(src->p);
+    const long long e = (long long)src->elem;
+    const auto* s = static_cast<const unsigned char*>(src->pop[src->cur]) + src_first * plane * e;
+    auto* d = static_cast<unsigned char*>(dst->pop[dst->cur]) + dst_first * plane * e;
+    return copy_rows(s, src->nn * e, d, dst->nn * e, count * plane * e, 2 * src->Q, dst->stream);
+}
+
+// Conservation sums of nodes [i0, i0 + n) of a population buffer whose
+// arrays are nn apart: per-thread compensated sums in the arithmetic type,
+// combined in FP64 in a fixed order (as in the whole-domain reduction).
+template <int Q, typename S, typename R>
+__global__ void __launch_bounds__(lbm::kReduceThreads) range_reduce_kernel(const S* __restrict__ pop, long long nn,
+                                                                          long long i0, long long n,
+                                                                          lbm::KParams<R> p,
+                                                                          double* __restrict__ partials) {
+    lbm::KahanT<R> acc[lbm::kSums];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+        R rho, jx, jy, jz, E;
+        lbm::node_moments<Q, S, R>(pop, nn, i0 + t, p, rho, jx, jy, jz, E);
+        acc[0].add(rho);
+        acc[1].add(jx);
+        acc[2].add(jy);
+        acc[3].add(jz);
+        acc[4].add(E);
+    }
+    __shared__ double sh[lbm::kSums][lbm::kReduceThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < lbm::kSums; ++q) {
+        double v = lbm::warp_sum((double)acc[q].s - (double)acc[q].c);
+        if (lane == 0) sh[q][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < lbm::kSums) {
+        lbm::Kahan b;
+        for (int w = 0; w < lbm::kReduceThreads / 32; ++w) b.add(sh[threadIdx.x][w]);
+        partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = b.s;
+    }
+}
+
+__global__ void __launch_bounds__(32) range_final_kernel(const double* __restrict__ partials, int nblocks,
+                                                         double* __restrict__ out) {
+    if (threadIdx.x < lbm::kSums) {
+        lbm::Kahan b;
+        for (int j = 0; j < nblocks; ++j) b.add(partials[(size_t)threadIdx.x * nblocks + j]);
+        out[threadIdx.x] = b.s;
+    }
+}
+
+template <int Q, typename S, typename R>
+int launch_range_sums(const lbm_handle* h, long long i0, long long n, double* partials, double* out) {
+    lbm::KParams<R> kp{};
+    kp.nn = h->nn;
+    kp.rho_ref = h->p.storage == LBM_STORE_FP16 ? (R)h->p.rho_ref : R(0);
+    kp.E_ref = h->p.storage == LBM_STORE_FP16 ? (R)h->p.E_ref : R(0);
+    range_reduce_kernel<Q, S, R><<<lbm::kReduceBlocks, lbm::kReduceThreads, 0, h->stream>>>(
+        (const S*)h->pop[h->cur], h->nn, i0, n, kp, partials);
+    range_final_kernel<<<1, 32, 0, h->stream>>>(partials, lbm::kReduceBlocks, out);
+    return cuda_error(cudaGetLastError(), "slab sums launch");
+}
+
+int range_sums(const lbm_handle* h, long long i0, long long n, double* partials, double* out) {
+    if (h->Q == 9) {
+        switch (h->p.storage) {
+            case LBM_STORE_FP64: return launch_range_sums<9, double, double>(h, i0, n, partials, out);
+            case LBM_STORE_FP32: return launch_range_sums<9, float, float>(h, i0, n, partials, out);
+            default: return launch_range_sums<9, __half, float>(h, i0, n, partials, out);
+        }
+    }
+    switch (h->p.storage) {
+        case LBM_STORE_FP64: return launch_range_sums<19, double, double>(h, i0, n, partials, out);
+        case LBM_STORE_FP32: return launch_range_sums<19, float, float>(h, i0, n, partials, out);
+        default: return launch_range_sums<19, __half, float>(h, i0, n, partials, out);
+    }
+}
+
+// global planes of slab s's local planes, in at most two runs (a periodic
+// domain wraps the first slab's lower halo to the top of the domain)
+struct Run {
+    int local, global, count;
+};
+std::vector<Run> local_runs(const lbm_slab& s, int nm) {
+    std::vector<Run> runs;
+    const int nl = s.lo + s.own + s.hi;
+    int j = 0;
+    while (j < nl) {
+        int g = ((s.first - s.lo + j) % nm + nm) % nm;
+        int len = nm - g < nl - j ? nm - g : nl - j;
+        runs.push_back({j, g, len});
+        j += len;
+    }
+    return runs;
+}
+
+int check_slabs(const lbm_slabs* s) {
+    if (!s) {
+        set_error("null slabs");
+        return LBM_ERR_INVALID_ARG;
+    }
+    return LBM_OK;
+}
+
+// halo planes of every slab from its neighbours' own planes
+int exchange(lbm_slabs* s) {
+    const int H = LBM_SLAB_HALO;
+    for (int i = 0; i < s->count; ++i) {
+        const lbm_slab& a = s->plan[i];
+        if (a.hi) {
+            const lbm_slab& b = s->plan[a.above];
+            if (int rc = copy_planes(s->h[i], a.lo + a.own, s->h[a.above], b.lo, H)) return rc;
+        }
+        if (a.lo) {
+            const lbm_slab& b = s->plan[a.below];
+            if (int rc = copy_planes(s->h[i], 0, s->h[a.below], b.lo + b.own - H, H)) return rc;
+        }
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_slab_plan(const lbm_params* p, int count, int i, lbm_slab* out) {
+    if (!p || !out) {
+        set_error("lbm_slab_plan: null argument");
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) {
+        set_error("lbm_slab_plan: lattice must be LBM_D2Q9 or LBM_D3Q19");
+        return LBM_ERR_INVALID_ARG;
+    }
+    const int nm = last_axis(*p);
+    if (count < 1 || i < 0 || i >= count) {
+        set_error("lbm_slab_plan: need count >= 1 and 0 <= i < count");
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (count > 1 && nm / count < LBM_SLAB_HALO) {
+        set_error("lbm_slab_plan: every slab must own at least " + std::to_string(LBM_SLAB_HALO) +
+                  " planes of the last axis (" + std::to_string(nm) + " planes into " + std::to_string(count) +
+                  " slabs)");
+        return LBM_ERR_INVALID_ARG;
+    }
+    std::memset(out, 0, sizeof(*out));
+    const int base = nm / count, extra = nm % count;
+    out->first = i * base + (i < extra ? i : extra);
+    out->own = base + (i < extra ? 1 : 0);
+    const bool periodic = p->wall == 0;
+    out->lo = count > 1 && (periodic || i > 0) ? LBM_SLAB_HALO : 0;
+    out->hi = count > 1 && (periodic || i < count - 1) ? LBM_SLAB_HALO : 0;
+    out->below = out->lo ? (i + count - 1) % count : -1;
+    out->above = out->hi ? (i + 1) % count : -1;
+    out->p = *p;
+    const int nl = out->lo + out->own + out->hi;
+    if (p->lattice == LBM_D2Q9)
+        out->p.ny = nl;
+    else
+        out->p.nz = nl;
+    // a cut is no wall: the fixed temperatures stay with the slabs at the ends
+    if (out->lo) out->p.T_fixed_lo = 0;
+    if (out->hi) out->p.T_fixed_hi = 0;
+    return LBM_OK;
+}
+
+int lbm_slabs_create(const lbm_params* p, int count, lbm_slabs** out) {
+    if (!p || !out) {
+        set_error("lbm_slabs_create: null argument");
+        return LBM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    lbm_slabs* s = new (std::nothrow) lbm_slabs();
+    if (!s) {
+        set_error("host allocation failed");
+        return LBM_ERR_OOM;
+    }
+    s->p = *p;
+    s->count = count;
+    s->D = p->lattice == LBM_D2Q9 ? 2 : 3;
+    s->plane = plane_nodes(*p);
+    s->nn = (long long)p->nx * p->ny * p->nz;
+    int rc = LBM_OK;
+    long long max_nl = 0;
+    for (int i = 0; i < count && !rc; ++i) {
+        lbm_slab sl;
+        rc = lbm_slab_plan(p, count, i, &sl);
+        if (rc) break;
+        s->plan.push_back(sl);
+        lbm_handle* h = nullptr;
+        rc = lbm_create(&sl.p, &h);
+        if (rc) break;
+        s->h.push_back(h);
+        const long long nl = sl.lo + sl.own + sl.hi;
+        if (nl > max_nl) max_nl = nl;
+    }
+    if (!rc) {
+        DeviceGuard dg(p->device);
+        rc = cuda_error(cudaMalloc((void**)&s->tmp, sizeof(double) * (size_t)(s->D + 3) * max_nl * s->plane),
+                        "slab field allocation");
+        if (!rc)
+            rc = cuda_error(cudaMalloc((void**)&s->partials,
+                                       sizeof(double) * (size_t)(lbm::kSums * lbm::kReduceBlocks + lbm::kSums)),
+                            "slab reduction scratch allocation");
+    }
+    if (rc) {
+        lbm_slabs_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return LBM_OK;
+}
+
+int lbm_slabs_count(const lbm_slabs* s) { return s ? s->count : LBM_ERR_INVALID_ARG; }
+
+lbm_handle* lbm_slabs_domain(lbm_slabs* s, int i) {
+    if (!s || i < 0 || i >= s->count) {
+        set_error("lbm_slabs_domain: no such slab");
+        return nullptr;
+    }
+    return s->h[i];
+}
+
+int lbm_slabs_init(lbm_slabs* s, const double* rho, const double* u, const double* eps, int mem) {
+    if (int rc = check_slabs(s)) return rc;
+    if (!rho || !u || !eps || (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE)) {
+        set_error("lbm_slabs_init: null field or bad mem flag");
+        return LBM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(s->p.device);
+    const int nm = last_axis(s->p);
+    const cudaMemcpyKind kind = mem == LBM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const size_t pb = sizeof(double) * (size_t)s->plane;
+    for (int i = 0; i < s->count; ++i) {
+        const lbm_slab& sl = s->plan[i];
+        lbm_handle* h = s->h[i];
+        const long long nl = h->nn;   // nodes of the slab's local domain
+        // fields of the slab's local planes (halos included) in its own layout
+        double* lr = s->tmp;
+        double* lu = s->tmp + nl;
+        double* le = s->tmp + (1 + s->D) * nl;
+        for (const Run& r : local_runs(sl, nm)) {
+            const size_t off_l = (size_t)r.local * s->plane, off_g = (size_t)r.global * s->plane;
+            int rc = cuda_error(cudaMemcpyAsync(lr + off_l, rho + off_g, pb * r.count, kind, h->stream), "slab init copy");
+            for (int c = 0; c < s->D && !rc; ++c)
+                rc = cuda_error(cudaMemcpyAsync(lu + c * nl + off_l, u + c * s->nn + off_g, pb * r.count, kind, h->stream),
+                                "slab init copy");
+            if (!rc)
+                rc = cuda_error(cudaMemcpyAsync(le + off_l, eps + off_g, pb * r.count, kind, h->stream), "slab init copy");
+            if (rc) return rc;
+        }
+        // synchronising: the next slab may reuse the field buffer afterwards
+        if (int rc = lbm_init(h, lr, lu, le, LBM_MEM_DEVICE)) return rc;
+    }
+    s->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_slabs_step(lbm_slabs* s, int n) {
+    if (int rc = check_slabs(s)) return rc;
+    if (n < 0) {
+        set_error("lbm_slabs_step: n < 0");
+        return LBM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(s->p.device);
+    for (int t = 0; t < n; ++t) {
+        for (int i = 0; i < s->count; ++i)
+            if (int rc = lbm_step(s->h[i], 1)) return rc;
+        if (int rc = exchange(s)) return rc;
+        ++s->steps;
+    }
+    return LBM_OK;
+}
+
+int lbm_slabs_moments(lbm_slabs* s, double* rho, double* u, double* T, double* P, int mem) {
+    if (int rc = check_slabs(s)) return rc;
+    if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) {
+        set_error("lbm_slabs_moments: bad mem flag");
+        return LBM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(s->p.device);
+    const cudaMemcpyKind kind = mem == LBM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const size_t pb = sizeof(double) * (size_t)s->plane;
+    int latched = LBM_OK;
+    for (int i = 0; i < s->count; ++i) {
+        const lbm_slab& sl = s->plan[i];
+        lbm_handle* h = s->h[i];
+        const long long nl = h->nn;
+        double* lr = s->tmp;
+        double* lu = s->tmp + nl;
+        double* lT = s->tmp + (1 + s->D) * nl;
+        double* lP = s->tmp + (2 + s->D) * nl;
+        int rc = lbm_moments(h, rho ? lr : nullptr, u ? lu : nullptr, T ? lT : nullptr, P ? lP : nullptr,
+                             LBM_MEM_DEVICE);
+        if (rc == LBM_ERR_NONPHYSICAL && !latched)
+            latched = rc;
+        else if (rc)
+            return rc;
+        // the slab's own planes into the whole-domain fields
+        const size_t off_l = (size_t)sl.lo * s->plane, off_g = (size_t)sl.first * s->plane, bytes = pb * sl.own;
+        if (rho) rc = cuda_error(cudaMemcpyAsync(rho + off_g, lr + off_l, bytes, kind, h->stream), "slab moments copy");
+        for (int c = 0; c < s->D && u && !rc; ++c)
+            rc = cuda_error(cudaMemcpyAsync(u + c * s->nn + off_g, lu + c * nl + off_l, bytes, kind, h->stream),
+                            "slab moments copy");
+        if (T && !rc) rc = cuda_error(cudaMemcpyAsync(T + off_g, lT + off_l, bytes, kind, h->stream), "slab moments copy");
+        if (P && !rc) rc = cuda_error(cudaMemcpyAsync(P + off_g, lP + off_l, bytes, kind, h->stream), "slab moments copy");
+        if (!rc) rc = cuda_error(cudaStreamSynchronize(h->stream), "stream synchronize");
+        if (rc) return rc;
+    }
+    return latched;
+}
+
+int lbm_slabs_diagnostics(lbm_slabs* s, double out[8]) {
+    if (int rc = check_slabs(s)) return rc;
+    if (!out) {
+        set_error("lbm_slabs_diagnostics: null output");
+        return LBM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(s->p.device);
+    double tot[lbm::kSums] = {0}, comp[lbm::kSums] = {0};   // Kahan sums over the slabs
+    double clamps = 0, bad = 0;
+    int latched = LBM_OK;
+    double* res = s->partials + lbm::kSums * lbm::kReduceBlocks;
+    for (int i = 0; i < s->count; ++i) {
+        const lbm_slab& sl = s->plan[i];
+        lbm_handle* h = s->h[i];
+        int rc = range_sums(h, (long long)sl.lo * s->plane, (long long)sl.own * s->plane, s->partials, res);
+        double sums[lbm::kSums];
+        lbm::Counters c;
+        if (!rc) rc = cuda_error(cudaMemcpyAsync(sums, res, sizeof(sums), cudaMemcpyDeviceToHost, h->stream), "slab sums copy");
+        if (!rc) rc = cuda_error(cudaMemcpyAsync(&c, h->cnt, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "slab counters copy");
+        if (rc) return rc;
+        rc = lbm_sync(h);   // waits for the copies; reports a latched device error
+        if (rc == LBM_ERR_NONPHYSICAL && !latched)
+            latched = rc;
+        else if (rc)
+            return rc;
+        for (int q = 0; q < lbm::kSums; ++q) {
+            const double y = sums[q] - comp[q], t = tot[q] + y;
+            comp[q] = (t - tot[q]) - y;
+            tot[q] = t;
+        }
+        clamps += (double)c.clamps;
+        bad += (double)c.bad;
+    }
+    for (int q = 0; q < lbm::kSums; ++q) out[q] = tot[q];
+    out[5] = clamps;
+    out[6] = bad;
+    out[7] = (double)s->steps;
+    return latched;
+}
+
+int lbm_slabs_sync(lbm_slabs* s) {
+    if (int rc = check_slabs(s)) return rc;
+    int latched = LBM_OK;
+    for (int i = 0; i < s->count; ++i) {
+        const int rc = lbm_sync(s->h[i]);
+        if (rc == LBM_ERR_NONPHYSICAL && !latched)
+            latched = rc;
+        else if (rc)
+            return rc;
+    }
+    return latched;
+}
+
+void lbm_slabs_destroy(lbm_slabs* s) {
+    if (!s) return;
+    {
+        DeviceGuard dg(s->p.device);
+        if (s->tmp) cudaFree(s->tmp);
+        if (s->partials) cudaFree(s->partials);
+    }
+    for (lbm_handle* h : s->h) lbm_destroy(h);
+    delete s;
+}
+
+size_t lbm_plane_bytes(const lbm_handle* h) {
+    if (!h) return 0;
+    return (size_t)2 * h->Q * (size_t)plane_nodes(h->p) * h->elem;
+}
+
+int lbm_get_planes(lbm_handle* h, int first, int count, void* buf, int mem) {
+    if (!h || !buf || (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE)) {
+        set_error("lbm_get_planes: null handle or buffer, or bad mem flag");
+        return LBM_ERR_INVALID_ARG;
+    }
+    const int nm = last_axis(h->p);
+    if (!h->initialised || first < 0 || count < 0 || first + count > nm) {
+        set_error("lbm_get_planes: no state, or planes outside [0, " + std::to_string(nm) + ")");
+        return LBM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(h->p.device);
+    const long long e = (long long)h->elem, width = count * plane_nodes(h->p) * e;
+    const auto* src = static_cast<const unsigned char*>(h->pop[h->cur]) + first * plane_nodes(h->p) * e;
+    if (mem == LBM_MEM_DEVICE) return copy_rows(src, h->nn * e, buf, width, width, 2 * h->Q, h->stream);
+    for (int r = 0; r < 2 * h->Q; ++r)
+        if (int rc = cuda_error(cudaMemcpyAsync(static_cast<unsigned char*>(buf) + r * width, src + r * h->nn * e,
+                                                (size_t)width, cudaMemcpyDeviceToHost, h->stream),
+                                "plane copy"))
+            return rc;
+    return cuda_error(cudaStreamSynchronize(h->stream), "stream synchronize");
+}
+
+int lbm_set_planes(lbm_handle* h, int first, int count, const void* buf, int mem) {
+    if (!h || !buf || (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE)) {
+        set_error("lbm_set_planes: null handle or buffer, or bad mem flag");
+        return LBM_ERR_INVALID_ARG;
+    }
+    const int nm = last_axis(h->p);
+    if (!h->initialised || first < 0 || count < 0 || first + count > nm) {
+        set_error("lbm_set_planes: no state, or planes outside [0, " + std::to_string(nm) + ")");
+        return LBM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(h->p.device);
+    const long long e = (long long)h->elem, width = count * plane_nodes(h->p) * e;
+    auto* dst = static_cast<unsigned char*>(h->pop[h->cur]) + first * plane_nodes(h->p) * e;
+    if (mem == LBM_MEM_DEVICE) return copy_rows(buf, width, dst, h->nn * e, width, 2 * h->Q, h->stream);
+    for (int r = 0; r < 2 * h->Q; ++r)
+        if (int rc = cuda_error(cudaMemcpyAsync(dst + r * h->nn * e, static_cast<const unsigned char*>(buf) + r * width,
+                                                (size_t)width, cudaMemcpyHostToDevice, h->stream),
+                                "plane copy"))
+            return rc;
+    return cuda_error(cudaStreamSynchronize(h->stream), "stream synchronize");
+}
+
+}  // extern "C"

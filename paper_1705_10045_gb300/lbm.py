@@ -42,7 +42,11 @@ EXPORTED = ("lbm_default_params", "lbm_create", "lbm_init", "lbm_step", "lbm_mom
             "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_status",
             "lbm_batch_set_budget", "lbm_batch_domain", "lbm_batch_size", "lbm_batch_variants",
             "lbm_batch_variant_name", "lbm_batch_set_variant", "lbm_batch_tune", "lbm_batch_sync",
-            "lbm_batch_destroy", "lbm_conservation_sums_noalloc", "lbm_coexistence")
+            "lbm_batch_destroy", "lbm_conservation_sums_noalloc", "lbm_coexistence", "lbm_slab_plan",
+            "lbm_slabs_create", "lbm_slabs_count", "lbm_slabs_domain", "lbm_slabs_init", "lbm_slabs_step",
+            "lbm_slabs_moments", "lbm_slabs_diagnostics", "lbm_slabs_sync", "lbm_slabs_destroy", "lbm_plane_bytes",
+            "lbm_get_planes", "lbm_set_planes")
+LBM_SLAB_HALO = 3
 
 
 class LbmError(RuntimeError):
@@ -66,6 +70,11 @@ class lbm_params(ctypes.Structure):
         ("step_kernel", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("device", ctypes.c_int),
     ]
+
+
+class lbm_slab(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_int), ("own", ctypes.c_int), ("lo", ctypes.c_int), ("hi", ctypes.c_int),
+                ("below", ctypes.c_int), ("above", ctypes.c_int), ("p", lbm_params)]
 
 
 _lib = None
@@ -134,6 +143,27 @@ def load(path: str = LIB_PATH):
     lib.lbm_batch_sync.argtypes = [B]
     lib.lbm_batch_destroy.argtypes = [B]
     lib.lbm_batch_destroy.restype = None
+    S = ctypes.c_void_p
+    lib.lbm_slab_plan.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(lbm_slab)]
+    lib.lbm_slabs_create.argtypes = [P, ctypes.c_int, ctypes.POINTER(S)]
+    lib.lbm_slabs_count.argtypes = [S]
+    lib.lbm_slabs_domain.argtypes = [S, ctypes.c_int]
+    lib.lbm_slabs_domain.restype = H
+    lib.lbm_slabs_init.argtypes = [S, dp, dp, dp, ctypes.c_int]
+    lib.lbm_slabs_step.argtypes = [S, ctypes.c_int]
+    lib.lbm_slabs_moments.argtypes = [S, dp, dp, dp, dp, ctypes.c_int]
+    lib.lbm_slabs_diagnostics.argtypes = [S, ctypes.POINTER(ctypes.c_double)]
+    lib.lbm_slabs_sync.argtypes = [S]
+    lib.lbm_slabs_destroy.argtypes = [S]
+    lib.lbm_slabs_destroy.restype = None
+    lib.lbm_plane_bytes.argtypes = [H]
+    lib.lbm_plane_bytes.restype = ctypes.c_size_t
+    lib.lbm_get_planes.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    lib.lbm_set_planes.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    for name in ("lbm_slab_plan", "lbm_slabs_create", "lbm_slabs_count", "lbm_slabs_init", "lbm_slabs_step",
+                 "lbm_slabs_moments", "lbm_slabs_diagnostics", "lbm_slabs_sync", "lbm_get_planes",
+                 "lbm_set_planes"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_status",
                  "lbm_batch_set_budget", "lbm_batch_size", "lbm_batch_variants", "lbm_batch_set_variant",
                  "lbm_batch_tune", "lbm_batch_sync"):
@@ -162,6 +192,20 @@ def _addr(a):
             raise TypeError("tensors must be contiguous float64")
         return a.data_ptr(), (LBM_MEM_DEVICE if a.is_cuda else LBM_MEM_HOST)
     raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _byte_addr(buf):
+    """(address, mem flag, bytes) of a contiguous uint8 numpy array or torch tensor."""
+    if isinstance(buf, np.ndarray):
+        if buf.dtype != np.uint8 or not buf.flags.c_contiguous:
+            raise TypeError("plane buffers must be C-contiguous uint8")
+        return buf.ctypes.data, LBM_MEM_HOST, buf.nbytes
+    import torch
+    if isinstance(buf, torch.Tensor):
+        if buf.dtype != torch.uint8 or not buf.is_contiguous():
+            raise TypeError("plane buffers must be contiguous uint8")
+        return buf.data_ptr(), (LBM_MEM_DEVICE if buf.is_cuda else LBM_MEM_HOST), buf.numel()
+    raise TypeError(f"unsupported buffer type {type(buf)}")
 
 
 def lbm_default_params() -> lbm_params:
@@ -280,6 +324,34 @@ def lbm_conservation_sums_noalloc(lattice: int, storage: int, nx: int, ny: int, 
                                                        ctypes.c_void_p(sums_ptr), ctypes.c_void_p(stream)))
 
 
+def lbm_slab_plan(params: lbm_params, count: int, i: int) -> lbm_slab:
+    """Plan of slab i of `count` along the last axis (host only, no device)."""
+    out = lbm_slab()
+    _check(load().lbm_slab_plan(ctypes.byref(params), int(count), int(i), ctypes.byref(out)))
+    return out
+
+
+def lbm_plane_bytes(h) -> int:
+    return int(load().lbm_plane_bytes(h))
+
+
+def lbm_get_planes(h, first: int, count: int, buf):
+    """Planes [first, first + count) of the populations into buf (2Q rows of
+    `count` planes, storage format); device buffers are filled asynchronously
+    on the handle's stream."""
+    a, mem, n = _byte_addr(buf)
+    if n < count * lbm_plane_bytes(h):
+        raise ValueError("plane buffer too small")
+    return _check(load().lbm_get_planes(h, int(first), int(count), a, mem))
+
+
+def lbm_set_planes(h, first: int, count: int, buf):
+    a, mem, n = _byte_addr(buf)
+    if n < count * lbm_plane_bytes(h):
+        raise ValueError("plane buffer too small")
+    return _check(load().lbm_set_planes(h, int(first), int(count), a, mem))
+
+
 class Lbm:
     """One simulation domain on the GPU (owns a liblbm handle)."""
 
@@ -323,6 +395,68 @@ class Lbm:
         if getattr(self, "h", None):
             lbm_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Slabs:
+    """One domain as `count` slabs along its last axis on one GPU
+    (lbm_slabs_*): same interface as Lbm, with the halo swap after every step."""
+
+    def __init__(self, count: int, **kw):
+        self.params = make_params(**kw)
+        s = ctypes.c_void_p()
+        _check(load().lbm_slabs_create(ctypes.byref(self.params), int(count), ctypes.byref(s)))
+        self.s = s
+        self.count = int(count)
+        self.Q = self.params.lattice
+        self.d = 2 if self.Q == LBM_D2Q9 else 3
+        self.shape = (self.params.nz, self.params.ny, self.params.nx)
+
+    def plan(self, i: int) -> lbm_slab:
+        return lbm_slab_plan(self.params, self.count, i)
+
+    def handle(self, i: int):
+        h = load().lbm_slabs_domain(self.s, int(i))
+        if not h:
+            raise LbmError(LBM_ERR_INVALID_ARG, load().lbm_last_error().decode())
+        return ctypes.c_void_p(h)
+
+    def init(self, rho, u, eps):
+        (r, m1), (uu, m2), (e, m3) = _addr(rho), _addr(u), _addr(eps)
+        if not (m1 == m2 == m3):
+            raise ValueError("rho, u and eps must all live on the host or all on the device")
+        return _check(load().lbm_slabs_init(self.s, r, uu, e, m1))
+
+    def step(self, n: int = 1):
+        return _check(load().lbm_slabs_step(self.s, int(n)))
+
+    def moments(self) -> dict:
+        out = {"rho": np.empty(self.shape), "u": np.empty((self.d,) + self.shape), "T": np.empty(self.shape),
+               "P": np.empty(self.shape)}
+        _check(load().lbm_slabs_moments(self.s, out["rho"].ctypes.data, out["u"].ctypes.data,
+                                        out["T"].ctypes.data, out["P"].ctypes.data, LBM_MEM_HOST))
+        return out
+
+    def diagnostics(self) -> dict:
+        o = (ctypes.c_double * 8)()
+        rc = load().lbm_slabs_diagnostics(self.s, o)
+        if rc not in (LBM_OK, LBM_ERR_NONPHYSICAL):
+            _check(rc)
+        return {"mass": o[0], "momentum": np.array(o[1:4]), "energy": o[4], "clamps": int(o[5]),
+                "bad": int(o[6]), "steps": int(o[7])}
+
+    def sync(self):
+        return _check(load().lbm_slabs_sync(self.s))
+
+    def close(self):
+        if getattr(self, "s", None):
+            load().lbm_slabs_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

@@ -1,0 +1,201 @@
+"""Slabs on the GPU (lbm_slabs_*, lbm_get_planes / lbm_set_planes, SlabRank):
+one domain cut along its last axis into slabs that swap three halo planes
+after every step.
+
+* FP32 and FP64 slabs reproduce the undivided domain bit for bit (same
+  per-node arithmetic), for 1 to 4 slabs, walls with a heated floor, latent
+  heat and gravity, a periodic axis where both halos of a slab come from one
+  neighbour, and both step forms; also at the full pool-boiling size.
+* FP64 slabs match the FP64 oracle to 1e-10.
+* FP16 slabs round with their own node keys: within the FP16 bounds of the
+  undivided run (the bounds of test_gpu_precision.py).
+* The sums over the owned planes equal the undivided domain's to rounding.
+* Plane copies round-trip through host and device buffers and reject planes
+  outside the slab.
+* Two processes on the same GPU, one slab each (SlabRank over gloo with host
+  staging), reproduce the undivided domain bit for bit.
+"""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+from gpu_helpers import max_abs, run_oracle
+from paper_1705_10045_gb300 import lbm
+from paper_1705_10045_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KEYS = ("rho", "u", "T", "P")
+
+
+def _walled3d():
+    f = W.spinodal((40, 24, 32), rho0=0.9, T0=0.8, noise=2e-2, seed=41)
+    kw = dict(lattice=19, nx=32, ny=24, nz=40, wall=1, T_fixed_lo=1, T_lo=0.86, T_fixed_hi=1, T_hi=0.78,
+              latent=0.02, gravity=(0.0, 0.0, -2e-5))
+    return f, kw, 200
+
+
+def _periodic2d():
+    f = W.spinodal((1, 60, 70), rho0=1.0, T0=0.8, noise=1e-2, seed=42)
+    return f, dict(lattice=9, nx=70, ny=60, nz=1), 300
+
+
+def _run_whole(f, steps, **kw):
+    sim = lbm.Lbm(**kw)
+    try:
+        sim.init(f.rho, np.ascontiguousarray(f.u[: sim.d]), sim.params.c_v * f.T)
+        sim.step(steps)
+        return sim.moments(), sim.diagnostics()
+    finally:
+        sim.close()
+
+
+def _run_slabs(f, steps, count, **kw):
+    s = lbm.Slabs(count, **kw)
+    try:
+        s.init(f.rho, np.ascontiguousarray(f.u[: s.d]), s.params.c_v * f.T)
+        s.step(steps)
+        return s.moments(), s.diagnostics()
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("count", [1, 2, 3, 4])
+@pytest.mark.parametrize("case", [_walled3d, _periodic2d])
+def test_fp32_slabs_equal_the_undivided_domain_bit_for_bit(case, count):
+    f, kw, steps = case()
+    kw = dict(kw, storage=lbm.LBM_STORE_FP32)
+    whole, dw = _run_whole(f, steps, **kw)
+    part, dp = _run_slabs(f, steps, count, **kw)
+    for k in KEYS:
+        assert np.array_equal(whole[k], part[k]), k
+    assert dp["steps"] == steps
+    assert dp["mass"] == pytest.approx(dw["mass"], rel=1e-12)
+    assert dp["energy"] == pytest.approx(dw["energy"], rel=1e-12)
+    assert np.allclose(dp["momentum"], dw["momentum"], rtol=0, atol=1e-9 * dw["mass"])
+
+
+@pytest.mark.parametrize("step_kernel", [lbm.LBM_STEP_FUSED, lbm.LBM_STEP_THREE_LAUNCH])
+def test_fp64_slabs_equal_the_undivided_domain_and_the_oracle(step_kernel):
+    f, kw, steps = _walled3d()
+    steps = 60
+    kw = dict(kw, storage=lbm.LBM_STORE_FP64, step_kernel=step_kernel)
+    whole, _ = _run_whole(f, steps, **kw)
+    part, _ = _run_slabs(f, steps, 3, **kw)
+    for k in KEYS:
+        assert np.array_equal(whole[k], part[k]), k
+    o = run_oracle(f, steps, **{k: v for k, v in kw.items() if k not in ("storage", "step_kernel")})
+    errs = {k: max_abs(part[k], o[k]) for k in KEYS}
+    assert all(v <= 1e-10 for v in errs.values()), errs
+
+
+def test_fp16_slabs_stay_within_the_fp16_bounds_of_the_undivided_run():
+    f, kw, steps = _periodic2d()
+    kw = dict(kw, storage=lbm.LBM_STORE_FP16)
+    whole, dw = _run_whole(f, steps, **kw)
+    part, dp = _run_slabs(f, steps, 3, **kw)
+    bounds = {"rho": 3e-2, "T": 1.5e-2, "u": 5e-3, "P": 5e-4}
+    errs = {k: max_abs(whole[k], part[k]) for k in KEYS}
+    assert all(errs[k] <= bounds[k] for k in KEYS), errs
+    assert dp["mass"] == pytest.approx(dw["mass"], rel=1e-4)
+
+
+def test_full_size_pool_boiling_in_slabs_equals_the_undivided_run():
+    sys.path.insert(0, ROOT)
+    import bench
+    f = bench._fields()
+    kw = dict(bench.PARAMS, storage=lbm.LBM_STORE_FP32)
+    steps = 6
+    whole, _ = _run_whole(f, steps, **kw)
+    for count in (2, 4):
+        part, _ = _run_slabs(f, steps, count, **kw)
+        for k in KEYS:
+            assert np.array_equal(whole[k], part[k]), (count, k)
+
+
+def test_plane_copies_round_trip_through_host_and_device_buffers():
+    import torch
+    f, kw, _ = _walled3d()
+    for storage in (lbm.LBM_STORE_FP64, lbm.LBM_STORE_FP32, lbm.LBM_STORE_FP16):
+        a = lbm.Lbm(**dict(kw, storage=storage))
+        b = lbm.Lbm(**dict(kw, storage=storage))
+        try:
+            a.init(f.rho, np.ascontiguousarray(f.u), 1.5 * f.T)
+            b.init(np.full_like(f.rho, 0.5), np.zeros_like(f.u), np.full_like(f.T, 1.2))
+            a.step(5)
+            pb = lbm.lbm_plane_bytes(a.h)
+            assert pb == 2 * 19 * 32 * 24 * {0: 8, 1: 4, 2: 2}[storage]
+            host = np.empty(7 * pb, dtype=np.uint8)
+            lbm.lbm_get_planes(a.h, 10, 7, host)
+            dev = torch.empty(7 * pb, dtype=torch.uint8, device="cuda")
+            lbm.lbm_get_planes(a.h, 10, 7, dev)
+            lbm.lbm_sync(a.h)
+            assert np.array_equal(host, dev.cpu().numpy())
+            # copy every plane of a into b, alternating host and device buffers
+            for first in range(0, 40, 8):
+                n = min(8, 40 - first)
+                if first % 16:
+                    buf = np.empty(n * pb, dtype=np.uint8)
+                else:
+                    buf = torch.empty(n * pb, dtype=torch.uint8, device="cuda")
+                lbm.lbm_get_planes(a.h, first, n, buf)
+                lbm.lbm_set_planes(b.h, first, n, buf)
+            lbm.lbm_sync(b.h)
+            sa, sb = a.get_state(), b.get_state()
+            assert np.array_equal(sa[16:], sb[16:])
+            for bad in ((38, 3), (-1, 2), (0, 41)):
+                with pytest.raises(lbm.LbmError) as e:
+                    lbm.lbm_get_planes(a.h, bad[0], bad[1], np.empty(max(bad[1], 1) * pb, dtype=np.uint8))
+                assert e.value.code == lbm.LBM_ERR_INVALID_ARG
+        finally:
+            a.close()
+            b.close()
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _slab_rank(rank, world, port, steps, out):
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    from paper_1705_10045_gb300.slabs import SlabRank
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        f, kw, _ = _walled3d()
+        r = SlabRank(dist, **dict(kw, storage=lbm.LBM_STORE_FP32))
+        try:
+            r.init(f.rho, f.u, 1.5 * f.T)
+            r.step(steps)
+            out[rank] = (r.slab.first, r.slab.own, r.moments())
+        finally:
+            r.close()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_slab_ranks_in_two_processes_equal_the_undivided_domain():
+    world, steps = 2, 80
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.spawn(_slab_rank, args=(world, _free_port(), steps, out), nprocs=world, join=True)
+        got = dict(out)
+    f, kw, _ = _walled3d()
+    whole, _ = _run_whole(f, steps, **dict(kw, storage=lbm.LBM_STORE_FP32))
+    for r in range(world):
+        first, own, m = got[r]
+        for k in KEYS:
+            ref = whole[k][:, first:first + own] if k == "u" else whole[k][first:first + own]
+            assert np.array_equal(ref, m[k]), (r, k)

@@ -1,0 +1,151 @@
+"""Slabs over processes on the CPU: gloo ranks each advance one slab of a
+domain (the plan of lbm_slab_plan) with the FP64 oracle as the per-slab
+step, and swap halos with exchange_halos after every step.  The owned planes,
+put back together, must equal the undivided oracle run bit for bit: this
+checks the halo depth (three planes per cut), the neighbour and tag pairing
+of the swap, the periodic wrap and the treatment of the cut ends (fixed wall
+temperatures only at the domain's walls) independently of the GPU.  A rank
+that leaves between steps makes its neighbour's next swap fail instead of
+hanging."""
+import datetime
+import os
+import socket
+import sys
+import time
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CASES = {
+    # D2Q9 periodic: two slabs, so both halos of a slab come from the same peer
+    "d2q9_periodic_2": dict(world=2, steps=40, p=dict(lattice=9, nx=24, ny=30)),
+    # D2Q9 walls, heated floor, cooled lid, latent heat, gravity: three slabs
+    "d2q9_walls_3": dict(world=3, steps=40, p=dict(lattice=9, nx=20, ny=33, wall=1, T_fixed_lo=1, T_lo=0.86,
+                                                  T_fixed_hi=1, T_hi=0.76, latent=0.02, gravity=(0, -2e-5, 0))),
+    # D3Q19 walls with a heated floor, variable conductivity
+    "d3q19_walls_2": dict(world=2, steps=12, p=dict(lattice=19, nx=8, ny=6, nz=16, wall=1, T_fixed_lo=1,
+                                                   T_lo=0.85, chi_mode=1, chi=0.05)),
+}
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _fields(p):
+    from paper_1705_10045_gb300 import workloads as W
+    Q = p["lattice"]
+    shape = (p.get("nz", 1), p["ny"], p["nx"])
+    f = W.spinodal(shape, rho0=0.9 if Q == 19 else 1.0, T0=0.8, noise=2e-2, seed=31)
+    return f.rho, f.u[: 2 if Q == 9 else 3], 1.5 * f.T
+
+
+def _oracle_params(lp):
+    """Oracle parameters from an lbm_params structure."""
+    import oracle
+    return oracle.Params(Q=lp.lattice, nx=lp.nx, ny=lp.ny, nz=lp.nz, kappa=lp.kappa, A=lp.A,
+                         barotropic=bool(lp.barotropic), T0=lp.T0, tau=lp.tau, tau_E=lp.tau_E, c_v=lp.c_v,
+                         chi_mode=bool(lp.chi_mode), lam=lp.lambda_, chi=lp.chi, g=tuple(lp.gravity),
+                         wall=bool(lp.wall), T_fixed_lo=bool(lp.T_fixed_lo), T_fixed_hi=bool(lp.T_fixed_hi),
+                         T_lo=lp.T_lo, T_hi=lp.T_hi, pressure_work=bool(lp.pressure_work),
+                         conduction=bool(lp.conduction), pseudoforce=bool(lp.pseudoforce), latent=lp.latent)
+
+
+def _plane_view(a, Q, first, count):
+    """Planes [first, first + count) of the last axis of a (Q, nz, ny, nx) array."""
+    return a[:, first:first + count] if Q == 19 else a[:, :, first:first + count]
+
+
+def _rank(rank, world, port, case, out, leave_after):
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1705_10045_gb300 import lbm
+    from paper_1705_10045_gb300.slabs import exchange_halos, local_planes
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    try:
+        cfg = CASES[case]
+        whole = lbm.make_params(**cfg["p"])
+        Q = whole.lattice
+        nm = whole.ny if Q == 9 else whole.nz
+        slab = lbm.lbm_slab_plan(whole, world, rank)
+        ax = 0 if Q == 19 else 1
+        rho, u, eps = _fields(cfg["p"])
+        st = oracle.State(_oracle_params(slab.p), local_planes(rho, slab, ax, nm), local_planes(u, slab, ax + 1, nm),
+                          local_planes(eps, slab, ax, nm))
+
+        def get(first, count):
+            return torch.from_numpy(np.ascontiguousarray(np.concatenate(
+                [_plane_view(st.N, Q, first, count), _plane_view(st.g, Q, first, count)])))
+
+        def put(first, count, t):
+            a = t.numpy()
+            _plane_view(st.N, Q, first, count)[...] = a[:Q]
+            _plane_view(st.g, Q, first, count)[...] = a[Q:]
+
+        for s in range(cfg["steps"]):
+            if leave_after is not None and rank == world - 1 and s == leave_after:
+                out[rank] = "left"
+                return          # leaves between steps: the process exits, its sockets close
+            st.step(1)
+            try:
+                exchange_halos(dist, slab, get, put)
+            except RuntimeError as e:
+                out[rank] = ("failed", s, str(e)[:200])
+                return
+        own = slice(slab.lo, slab.lo + slab.own)
+        out[rank] = (slab.first, slab.own, _plane_view(st.N, Q, slab.lo, slab.own).copy(),
+                     _plane_view(st.g, Q, slab.lo, slab.own).copy())
+        del own
+    finally:
+        if leave_after is None:
+            dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_slabs_on_gloo_ranks_equal_the_undivided_oracle_bit_for_bit(case):
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1705_10045_gb300 import lbm
+    cfg = CASES[case]
+    world = cfg["world"]
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, _free_port(), case, out, None), nprocs=world, join=True)
+        got = dict(out)
+    whole = lbm.make_params(**cfg["p"])
+    Q = whole.lattice
+    ref = oracle.State(_oracle_params(whole), *_fields(cfg["p"]))
+    ref.step(cfg["steps"])
+    N = np.full_like(ref.N, np.nan)
+    g = np.full_like(ref.g, np.nan)
+    for r in range(world):
+        first, own, n, e = got[r]
+        _plane_view(N, Q, first, own)[...] = n
+        _plane_view(g, Q, first, own)[...] = e
+    assert np.array_equal(N, ref.N) and np.array_equal(g, ref.g)
+    # the run moved: the state is not the initial one
+    init = oracle.State(_oracle_params(whole), *_fields(cfg["p"]))
+    assert not np.array_equal(init.N, ref.N)
+
+
+def test_a_rank_that_leaves_makes_its_neighbours_swap_fail_not_hang():
+    world, leave_after = 2, 5
+    t0 = time.monotonic()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, _free_port(), "d2q9_periodic_2", out, leave_after), nprocs=world, join=True)
+        got = dict(out)
+    assert got[1] == "left"
+    status, step, _ = got[0]
+    assert status == "failed" and step == leave_after
+    assert time.monotonic() - t0 < 60

@@ -261,6 +261,36 @@ def storage_leg(storage: int, steps: int, rho_h, u_h, eps_h, stream, dev) -> dic
             "bad_nodes": diag["bad"]}
 
 
+def slabs_leg(count: int, steps: int, rho_h, u_h, eps_h, stream, dev) -> dict:
+    """The headline workload cut into `count` slabs along z on this GPU
+    (lbm_slabs_*): every slab steps, then three halo planes per cut are
+    copied from the neighbours.  Measures what the decomposition costs on one
+    device: the halo planes stepped twice and the copies."""
+    import torch
+    from paper_1705_10045_gb300 import lbm
+    s = lbm.Slabs(count, storage=lbm.LBM_STORE_FP32, device=dev, stream=stream.cuda_stream, **PARAMS)
+    try:
+        s.init(rho_h, u_h, eps_h)
+        s.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        diag = s.diagnostics()
+        plans = [s.plan(i) for i in range(count)]
+    finally:
+        s.close()
+    nn = NX * NY * NZ
+    halo = sum(p.lo + p.hi for p in plans)
+    plane_bytes = 2 * 19 * 4 * NX * NY
+    return {"slabs": count, "value": nn / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": steps,
+            "halo_planes_stepped": halo, "halo_bytes_copied_per_step": halo * plane_bytes,
+            "launches_per_step": count + halo // lbm.LBM_SLAB_HALO, "bad_nodes": diag["bad"]}
+
+
 def batched_bench(count: int = 256, steps: int = BATCH_STEPS):
     """Many uneven D2Q9 droplet domains, FP32: square sides uniform in
     {64, 96, ..., 512}, T uniform in [0.7, 0.95], radius uniform in
@@ -379,6 +409,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-domains measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--no-storage-legs", action="store_true", help="skip the FP16 and FP64 storage legs")
+    ap.add_argument("--no-slabs", action="store_true", help="skip the slab-decomposition measurement")
     ap.add_argument("--serve-jobs", type=int, default=24)
     ap.add_argument("--size", default=None, help="NXxNYxNZ of a smaller pool-boiling box (profiling)")
     args = ap.parse_args()
@@ -458,6 +489,9 @@ def main():
         extra_storage["fp16_storage"] = storage_leg(lbm.LBM_STORE_FP16, min(args.steps, 200), rho_h, u_h, eps_h,
                                                     stream, dev)
         extra_storage["fp64"] = storage_leg(lbm.LBM_STORE_FP64, min(args.steps, 10), rho_h, u_h, eps_h, stream, dev)
+    if not args.no_slabs:
+        extra_storage["slabs_on_one_gpu"] = [slabs_leg(c, min(args.steps, 100), rho_h, u_h, eps_h, stream, dev)
+                                             for c in (2, 4)]
 
     if rank == 0:
         peak, peak_kind = _peak()

@@ -153,6 +153,12 @@ int lbm_step(lbm_handle* h, int n);
  * latched device error if any. */
 int lbm_moments(lbm_handle* h, double* rho, double* u, double* T, double* P, int mem);
 
+/* FP32 twin of lbm_moments: the same fields, computed as lbm_moments does
+ * and rounded to the nearest float (half the bytes to move).  Host output
+ * is staged through the handle's second population buffer, which the next
+ * step overwrites anyway.  Synchronising; errors as lbm_moments. */
+int lbm_moments_f(lbm_handle* h, float* rho, float* u, float* T, float* P, int mem);
+
 /* Global sums of the current state, reduced in FP64 with Kahan compensation in
  * a fixed order (bitwise reproducible): out[0] mass, out[1..3] momentum
  * sum c_k N_k (x, y, z), out[4] internal energy, out[5] clamped nodes (U >= 0)

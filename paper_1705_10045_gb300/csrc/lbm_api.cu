@@ -1,6 +1,7 @@
 // C-ABI of liblbm (declared in include/lbm.h): parameter validation, device
 // memory, host/device transfers, error latching and dispatch to the
 // per-lattice back ends.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -92,6 +93,12 @@ int be_moments(lbm_handle* h, double* r, double* u, double* T, double* P) {
 }
 int be_reduce(lbm_handle* h, double* out) {
     return h->Q == 9 ? lbm::Backend<9>::reduce(h, out) : lbm::Backend<19>::reduce(h, out);
+}
+
+// FP64 -> FP32, round to nearest (the FP32 twin of the moments)
+__global__ void narrow_kernel(const double* __restrict__ src, float* __restrict__ dst, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
 }
 
 // Wait for the stream and report non-physical nodes counted since the last report.
@@ -318,6 +325,45 @@ int lbm_moments(lbm_handle* h, double* rho, double* u, double* T, double* P, int
         return rc;
     if (P && (rc = cuda_error(cudaMemcpyAsync(P, dP, plane, cudaMemcpyDeviceToHost, h->stream), "moments copy")))
         return rc;
+    return sync_and_latch(h);
+}
+
+int lbm_moments_f(lbm_handle* h, float* rho, float* u, float* T, float* P, int mem) {
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = need_init(h)) return rc;
+    if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) {
+        set_error("lbm_moments_f: bad mem flag");
+        return LBM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(h->p.device);
+    int rc;
+    if ((rc = ensure_staging(h))) return rc;
+    const long long nn = h->nn;
+    double* s = h->staging;
+    double *dr = rho ? s : nullptr, *du = u ? s + nn : nullptr, *dT = T ? s + (1 + h->D) * nn : nullptr,
+           *dP = P ? s + (2 + h->D) * nn : nullptr;
+    if ((rc = be_moments(h, dr, du, dT, dP))) return rc;
+    // the floats: straight into device outputs, or into the idle population
+    // buffer (at least (d + 3) floats per node in every storage format)
+    float* idle = static_cast<float*>(h->pop[h->cur ^ 1]);
+    struct Field {
+        const double* src;
+        float* dst;
+        long long n;
+    } fields[4] = {{dr, rho, nn}, {du, u, h->D * nn}, {dT, T, nn}, {dP, P, nn}};
+    long long off = 0;
+    for (const Field& f : fields) {
+        if (!f.dst) continue;
+        float* d = mem == LBM_MEM_DEVICE ? f.dst : idle + off;
+        const unsigned blocks = (unsigned)std::min<long long>((f.n + 255) / 256, 4096);
+        narrow_kernel<<<blocks, 256, 0, h->stream>>>(f.src, d, f.n);
+        if ((rc = cuda_error(cudaGetLastError(), "moments narrowing launch"))) return rc;
+        if (mem == LBM_MEM_HOST &&
+            (rc = cuda_error(cudaMemcpyAsync(f.dst, d, sizeof(float) * (size_t)f.n, cudaMemcpyDeviceToHost, h->stream),
+                             "moments copy")))
+            return rc;
+        off += f.n;
+    }
     return sync_and_latch(h);
 }
 

@@ -45,7 +45,7 @@ EXPORTED = ("lbm_default_params", "lbm_create", "lbm_init", "lbm_step", "lbm_mom
             "lbm_batch_destroy", "lbm_conservation_sums_noalloc", "lbm_coexistence", "lbm_slab_plan",
             "lbm_slabs_create", "lbm_slabs_count", "lbm_slabs_domain", "lbm_slabs_init", "lbm_slabs_step",
             "lbm_slabs_moments", "lbm_slabs_diagnostics", "lbm_slabs_sync", "lbm_slabs_destroy", "lbm_plane_bytes",
-            "lbm_get_planes", "lbm_set_planes")
+            "lbm_get_planes", "lbm_set_planes", "lbm_moments_f")
 LBM_SLAB_HALO = 3
 
 
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_init.argtypes = [H, dp, dp, dp, ctypes.c_int]
     lib.lbm_step.argtypes = [H, ctypes.c_int]
     lib.lbm_moments.argtypes = [H, dp, dp, dp, dp, ctypes.c_int]
+    lib.lbm_moments_f.argtypes = [H, dp, dp, dp, dp, ctypes.c_int]
+    lib.lbm_moments_f.restype = ctypes.c_int
     lib.lbm_diagnostics.argtypes = [H, ctypes.POINTER(ctypes.c_double)]
     lib.lbm_state_bytes.argtypes = [H]
     lib.lbm_state_bytes.restype = ctypes.c_size_t
@@ -262,6 +264,32 @@ def lbm_moments(h, rho=None, u=None, T=None, P=None):
         raise ValueError("outputs must all live on the host or all on the device")
     mem = mems.pop() if mems else LBM_MEM_HOST
     return _check(load().lbm_moments(h, *[a for a, _ in addrs], mem))
+
+
+def _addr_f32(a):
+    """(address, mem flag) of a float32 numpy array or torch tensor."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags.c_contiguous:
+            raise TypeError("host arrays must be C-contiguous float32")
+        return a.ctypes.data, LBM_MEM_HOST
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float32")
+        return a.data_ptr(), (LBM_MEM_DEVICE if a.is_cuda else LBM_MEM_HOST)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def lbm_moments_f(h, rho=None, u=None, T=None, P=None):
+    """FP32 twin of lbm_moments (float32 outputs, host or device)."""
+    addrs = [_addr_f32(a) for a in (rho, u, T, P)]
+    mems = {m for _, m in addrs if m is not None}
+    if len(mems) > 1:
+        raise ValueError("outputs must all live on the host or all on the device")
+    mem = mems.pop() if mems else LBM_MEM_HOST
+    return _check(load().lbm_moments_f(h, *[a for a, _ in addrs], mem))
 
 
 def lbm_diagnostics(h) -> np.ndarray:

@@ -68,6 +68,11 @@ def test_create_rejects_unstable_conduction(libpath):
 def test_null_handle_calls_fail_cleanly(libpath):
     L = lbm.load()
     assert L.lbm_step(None, 1) == lbm.LBM_ERR_INVALID_ARG
+    assert L.lbm_moments_f(None, None, None, None, None, lbm.LBM_MEM_HOST) == lbm.LBM_ERR_INVALID_ARG
+    assert L.lbm_slabs_step(None, 1) == lbm.LBM_ERR_INVALID_ARG
+    assert L.lbm_get_planes(None, 0, 1, None, lbm.LBM_MEM_HOST) == lbm.LBM_ERR_INVALID_ARG
+    assert L.lbm_plane_bytes(None) == 0
+    L.lbm_slabs_destroy(None)
     assert L.lbm_sync(None) == lbm.LBM_ERR_INVALID_ARG
     assert L.lbm_state_bytes(None) == 0
     L.lbm_destroy(None)

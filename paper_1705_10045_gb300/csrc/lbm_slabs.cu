@@ -271,6 +271,12 @@ int lbm_slabs_create(const lbm_params* p, int count, lbm_slabs** out) {
         return LBM_ERR_INVALID_ARG;
     }
     *out = nullptr;
+    lbm_slab first;
+    if (count < 1) {
+        set_error("lbm_slabs_create: need count >= 1");
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (int rc = lbm_slab_plan(p, count, 0, &first)) return rc;   // rejects thin slabs before any allocation
     lbm_slabs* s = new (std::nothrow) lbm_slabs();
     if (!s) {
         set_error("host allocation failed");

@@ -68,3 +68,12 @@ def test_plan_rejects_bad_counts_and_thin_slabs(count, i):
         lbm.lbm_slab_plan(p, count, i)
     assert e.value.code == lbm.LBM_ERR_INVALID_ARG
     assert lbm.lbm_slab_plan(lbm.make_params(lattice=19, nx=4, ny=4, nz=14), 4, 3).own == 3
+
+
+@pytest.mark.parametrize("count", [0, -1, 5])
+def test_slabs_create_rejects_bad_counts_before_touching_a_device(count):
+    import ctypes
+    p = lbm.make_params(lattice=19, nx=4, ny=4, nz=11)
+    s = ctypes.c_void_p()
+    assert lbm.load().lbm_slabs_create(ctypes.byref(p), count, ctypes.byref(s)) == lbm.LBM_ERR_INVALID_ARG
+    assert not s.value

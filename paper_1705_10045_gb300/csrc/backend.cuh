@@ -38,18 +38,20 @@ inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + thre
 
 // CTA shape of the fused kernel: a TX x TY tile of consumer threads plus NP
 // producer threads.  D3Q19 uses 32 x 8 nodes with 128 producers (two CTAs per
-// SM) in FP32/FP16 and 256 producers in FP64; D2Q9 rows of 64.
+// SM) in FP32/FP16 and 256 producers in FP64.  D2Q9 uses rows of 128 nodes
+// with 160 producers: one producer per node of the 132-node ring row, so the
+// moments of a row take a single round of loads.
 template <int Q, typename R> struct FusedTile;
-template <typename R> struct FusedTile<9, R> { static constexpr int TX = 64, TY = 1, NP = 64; };
+template <typename R> struct FusedTile<9, R> { static constexpr int TX = 128, TY = 1, NP = 160; };
 template <> struct FusedTile<19, float> { static constexpr int TX = 32, TY = 8, NP = 128; };
 template <> struct FusedTile<19, double> { static constexpr int TX = 32, TY = 8, NP = 256; };
 
 // CTA shapes a batch may run with (TX x TY consumers + NP producers); the
 // autotuner times each on the batch and keeps the fastest.
 template <int Q, typename R, int V> struct BatchShape;
-template <typename R> struct BatchShape<9, R, 0> { static constexpr int TX = 64, TY = 1, NP = 64; };
+template <typename R> struct BatchShape<9, R, 0> { static constexpr int TX = 128, TY = 1, NP = 160; };
 template <typename R> struct BatchShape<9, R, 1> { static constexpr int TX = 32, TY = 1, NP = 32; };
-template <typename R> struct BatchShape<9, R, 2> { static constexpr int TX = 128, TY = 1, NP = 64; };
+template <typename R> struct BatchShape<9, R, 2> { static constexpr int TX = 64, TY = 1, NP = 64; };
 template <typename R> struct BatchShape<19, R, 0> { static constexpr int TX = 32, TY = 8, NP = 128; };
 template <typename R> struct BatchShape<19, R, 1> { static constexpr int TX = 32, TY = 8, NP = 160; };
 template <typename R> struct BatchShape<19, R, 2> { static constexpr int TX = 32, TY = 4, NP = 96; };
@@ -306,7 +308,7 @@ template <int Q> int Backend<Q>::reduce(lbm_handle* h, double* out_dev) { LBM_DI
     }
 template <int Q> int Backend<Q>::batch_variants() { return 3; }
 template <int Q> const char* Backend<Q>::batch_variant_name(int v) {
-    static const char* n9[] = {"64x1+64", "32x1+32", "128x1+64"};
+    static const char* n9[] = {"128x1+160", "32x1+32", "64x1+64"};
     static const char* n19[] = {"32x8+128", "32x8+160", "32x4+96"};
     if (v < 0 || v > 2) return "";
     return Q == 9 ? n9[v] : n19[v];

@@ -291,6 +291,42 @@ def slabs_leg(count: int, steps: int, rho_h, u_h, eps_h, stream, dev) -> dict:
             "launches_per_step": count + halo // lbm.LBM_SLAB_HALO, "bad_nodes": diag["bad"]}
 
 
+D2Q9_NX, D2Q9_NY = 8192, 4608
+
+
+def d2q9_leg(steps: int, stream, dev) -> dict:
+    """One large D2Q9 domain, FP32: 8192 x 4608 nodes (as many as the D3Q19
+    workload), periodic, a liquid slab 4096 nodes across x in its vapour at
+    T = 0.8, +-1e-4 noise (144 B per lattice update)."""
+    import torch
+    from paper_1705_10045_gb300 import lbm
+    from paper_1705_10045_gb300 import workloads as W
+    f = W.flat_slab_2d(nx=D2Q9_NX, ny=D2Q9_NY, T=0.8, slab=D2Q9_NX // 2, noise=1e-4)
+    sim = lbm.Lbm(lattice=9, nx=D2Q9_NX, ny=D2Q9_NY, nz=1, storage=lbm.LBM_STORE_FP32, device=dev,
+                  stream=stream.cuda_stream, kappa=0.01, A=-0.152, tau=1.0, tau_E=1.0, c_v=1.5, lambda_=0.05)
+    try:
+        sim.init(f.rho, np.ascontiguousarray(f.u[:2]), 1.5 * f.T)
+        del f
+        sim.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        diag = sim.diagnostics()
+    finally:
+        sim.close()
+    nn = D2Q9_NX * D2Q9_NY
+    peak, kind = _peak()
+    gbs = 144 * nn / (ms * 1e-3) / 1e9
+    return {"workload": f"D2Q9 FP32 {D2Q9_NX}x{D2Q9_NY}, periodic, liquid slab across x in vapour at T=0.8",
+            "value": nn / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": steps,
+            "algorithmic_bytes_per_node": 144, "achieved_gbs": gbs, "frac": gbs / peak, "peak_kind": kind,
+            "bad_nodes": diag["bad"]}
+
+
 def batched_bench(count: int = 256, steps: int = BATCH_STEPS):
     """Many uneven D2Q9 droplet domains, FP32: square sides uniform in
     {64, 96, ..., 512}, T uniform in [0.7, 0.95], radius uniform in
@@ -410,6 +446,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--no-storage-legs", action="store_true", help="skip the FP16 and FP64 storage legs")
     ap.add_argument("--no-slabs", action="store_true", help="skip the slab-decomposition measurement")
+    ap.add_argument("--no-d2q9", action="store_true", help="skip the single-domain D2Q9 measurement")
     ap.add_argument("--serve-jobs", type=int, default=24)
     ap.add_argument("--size", default=None, help="NXxNYxNZ of a smaller pool-boiling box (profiling)")
     args = ap.parse_args()
@@ -489,6 +526,8 @@ def main():
         extra_storage["fp16_storage"] = storage_leg(lbm.LBM_STORE_FP16, min(args.steps, 200), rho_h, u_h, eps_h,
                                                     stream, dev)
         extra_storage["fp64"] = storage_leg(lbm.LBM_STORE_FP64, min(args.steps, 10), rho_h, u_h, eps_h, stream, dev)
+    if not args.no_d2q9:
+        extra_storage["d2q9_fp32"] = d2q9_leg(min(args.steps, 200), stream, dev)
     if not args.no_slabs:
         extra_storage["slabs_on_one_gpu"] = [slabs_leg(c, min(args.steps, 100), rho_h, u_h, eps_h, stream, dev)
                                              for c in (2, 4)]

@@ -447,11 +447,15 @@ def main():
     ap.add_argument("--no-storage-legs", action="store_true", help="skip the FP16 and FP64 storage legs")
     ap.add_argument("--no-slabs", action="store_true", help="skip the slab-decomposition measurement")
     ap.add_argument("--no-d2q9", action="store_true", help="skip the single-domain D2Q9 measurement")
+    ap.add_argument("--d2q9-size", default=None, help="NXxNY of a smaller D2Q9 domain (profiling)")
     ap.add_argument("--serve-jobs", type=int, default=24)
     ap.add_argument("--size", default=None, help="NXxNYxNZ of a smaller pool-boiling box (profiling)")
     args = ap.parse_args()
     if args.size:
         _set_size(args.size)
+    if args.d2q9_size:
+        global D2Q9_NX, D2Q9_NY
+        D2Q9_NX, D2Q9_NY = (int(v) for v in args.d2q9_size.lower().split("x"))
     if args.impl == "reference":
         return run_reference(args)
 

@@ -515,11 +515,22 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    t0 = time.perf_counter()
-    sim.init(rho_h, u_h, eps_h)
-    sim.step(args.steps)
-    lbm.lbm_moments(sim.h, out["rho"], out["u"], out["T"], out["P"])
-    e2e_s = time.perf_counter() - t0
+    # events around the steps and host clock marks split the end-to-end time
+    # into init (fields in), steps and moments (fields out); clocks sampled
+    # over the whole leg
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as e2e_clk:
+        t0 = time.perf_counter()
+        sim.init(rho_h, u_h, eps_h)
+        t_init = time.perf_counter()
+        s0.record(stream)
+        sim.step(args.steps)
+        s1.record(stream)
+        lbm.lbm_moments(sim.h, out["rho"], out["u"], out["T"], out["P"])
+        e2e_s = time.perf_counter() - t0
+    e2e_parts = {"init_ms": (t_init - t0) * 1e3, "steps_ms_per_step": s0.elapsed_time(s1) / args.steps,
+                 "moments_ms": (e2e_s - (t_init - t0)) * 1e3 - s0.elapsed_time(s1), "clocks": e2e_clk.summary()}
     if dist:
         e2e_s = max_over_ranks(e2e_s, dist)
     h2d = (rho_h.numel() + u_h.numel() + eps_h.numel()) * 8
@@ -561,7 +572,8 @@ def main():
                          "step_frac": 4 * 19 * 4 * nn / (ms / args.steps * 1e-3) / 1e9 / peak,
                          "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
             "e2e": {"value": whole_job_mlups(nn, args.steps, ws, e2e_s), "unit": "MLUPS",
-                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "parts": e2e_parts},
             "gpu_launches": launches * args.steps,
             "clocks": clk.summary(),
             "diagnostics": {"mass": diag["mass"], "energy": diag["energy"], "clamps": diag["clamps"],

@@ -233,6 +233,18 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         const bool walls = p->wall;
         const int nm = G.nm;
         const R third = R(1.0 / 3.0);
+        // the node's g populations first: their loads are in flight while the
+        // finite differences below read shared memory
+        const int n = c * plane_n + n_ab;
+        R hv[Q];
+        {
+            const S* qg = src + n + (size_t)Q * nn;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                hv[k] = Store<S, R>::load(qg, 0, R(V::w(k)) * p->E_ref);
+                qg += nn;
+            }
+        }
         const int sr = slotn(c, Sh::kRutSlots), sd = slotn(c, Sh::kDuSlots);
         const int fc = (tb + FB) * FW + ta + 1;        // 1-ring index of the node
         const R rho = rut(sr, 0, fc), T = rut(sr, 4, fc);
@@ -273,19 +285,12 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         if (p->latent != R(0)) dE += latent_heat(*p, rho, T, div);
         if (P - rho * third >= R(0)) atomicAdd(&cnt->clamps, 1ull);
 
-        const int n = c * plane_n + n_ab;
-        // the node's population k sits at qn + k nn (N) and qn + (Q + k) nn (g);
-        // the pointers walk from one population to the next
+        // the node's N population k sits at qn + k nn; the pointer walks from
+        // one population to the next
         const S* qn = src + n;
-        const S* qg = qn + (size_t)Q * nn;
-        R hv[Q];
         R E = 0;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            hv[k] = Store<S, R>::load(qg, 0, R(V::w(k)) * p->E_ref);
-            E += hv[k];
-            qg += nn;
-        }
+        for (int k = 0; k < Q; ++k) E += hv[k];
         if (!(finite_pos(rho) && finite_pos(E))) atomicAdd(&cnt->bad, 1ull);
         const R dEoverE = dE / E;
         // node offsets of x + c_k: +-1 along a and b (periodic), along the

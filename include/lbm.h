@@ -51,12 +51,19 @@ extern "C" {
 #define LBM_ERR_INVALID_ARG (-1)
 #define LBM_ERR_UNSTABLE_PARAMS (-2)
 #define LBM_ERR_OOM (-3)
-/* A CUDA call failed, or a wait inside the fused step gave up (the producer
- * and consumer warps of a CTA hand planes over through shared-memory
- * barriers whose waits are bounded to about half a second); the state of the
- * steps since the last synchronising call is then not valid. */
+/* A CUDA call failed; the state of the steps since the last synchronising
+ * call is then not valid. */
 #define LBM_ERR_CUDA (-4)
 #define LBM_ERR_NONPHYSICAL (-5)
+/* A wait inside the fused step gave up: the producer and consumer warps of a
+ * CTA hand planes over through shared-memory barriers whose waits are
+ * bounded to about half a second, after which the CTA finishes without
+ * waiting and counts the timeout.  Every synchronising call reports it until
+ * lbm_init or lbm_set_state gives the handle a new state.  For tests, the
+ * environment variable LBM_FAULT_DROP_HANDOFF=<plane>, read by lbm_create,
+ * makes the first CTA of every fused step of that handle withhold the
+ * hand-off of that plane, so that the wait runs out. */
+#define LBM_ERR_TIMEOUT (-6)
 
 #define LBM_D2Q9 9
 #define LBM_D3Q19 19

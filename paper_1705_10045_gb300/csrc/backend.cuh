@@ -84,8 +84,15 @@ template <int Q, typename S, typename R> struct Impl {
             h->fused_ready = true;
         }
         const dim3 grid((G.na + TX - 1) / TX, (G.nb + TY - 1) / TY, (G.nm + G.chunk - 1) / G.chunk);
-        kern<<<grid, TX * TY + NP, smem, h->stream>>>((const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], kp, G,
-                                                 (Counters*)h->cnt);
+        if (h->fault_drop > 0) {   // fault-injection test hook (LBM_FAULT_DROP_HANDOFF)
+            auto fk = fused_step_fault_kernel<Q, S, R, TX, TY, NP>;
+            cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            fk<<<grid, TX * TY + NP, smem, h->stream>>>((const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], kp, G,
+                                                        (Counters*)h->cnt, h->fault_drop - 1);
+        } else {
+            kern<<<grid, TX * TY + NP, smem, h->stream>>>((const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], kp, G,
+                                                     (Counters*)h->cnt);
+        }
         h->cur ^= 1;
     }
 

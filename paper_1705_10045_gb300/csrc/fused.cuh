@@ -371,10 +371,12 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
 // One CTA of the producer/consumer fused step: the tile (a0, b0) of planes
 // [zb, zb + G.chunk) of one domain.  Threads [0, TX*TY) are consumers (one per
 // tile node), threads [TX*TY, TX*TY + NP) producers.
-template <int Q, typename S, typename R, int TX, int TY, int NP>
+// FAULT instantiates the fault-injection form: the first CTA withholds the
+// hand-off of plane fault_plane (tests of the bounded waits only).
+template <int Q, typename S, typename R, int TX, int TY, int NP, bool FAULT = false>
 __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restrict__ dst, const KParams<R>* p,
                                            const MarchGeom& G, unsigned step, int a0, int b0, int zb,
-                                           Counters* cnt, unsigned char* smem_raw) {
+                                           Counters* cnt, unsigned char* smem_raw, int fault_plane = -1) {
     using St = FusedStages<Q, S, R, TX, TY>;
     using Sh = typename St::Sh;
     constexpr int NC = TX * TY, NT = NC + NP;
@@ -439,7 +441,9 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restr
             const bool f_need = f >= zb - 1 && f <= ze && (walls ? (f >= 0 && f < G.nm) : true);
             if (f_need) st.f_stage(f, t, NP);
             asm volatile("bar.sync 1, %0;" ::"r"(NP));
-            if (t == 0) mbar_arrive(full + ((i - zb + 2) % D));
+            bool withhold = false;
+            if constexpr (FAULT) withhold = i == fault_plane && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+            if (t == 0 && !withhold) mbar_arrive(full + ((i - zb + 2) % D));
         }
     } else {
         // consumers: C(c) needs M(c+2) and F(c+1), i.e. producer iteration c+2
@@ -465,6 +469,19 @@ __global__ void __launch_bounds__(TX* TY + NP) fused_step_kernel(const S* __rest
     extern __shared__ __align__(16) unsigned char smem_raw[];
     fused_tile<Q, S, R, TX, TY, NP>(src, dst, &p, G, p.step, blockIdx.x * TX, blockIdx.y * TY,
                                     blockIdx.z * G.chunk, cnt, smem_raw);
+}
+
+// The same step with the fault-injection hook: the first CTA withholds the
+// hand-off of plane fault_plane, so that its consumers' bounded wait runs out
+// and the timeout is counted.  Launched only for handles created with
+// LBM_FAULT_DROP_HANDOFF set; the kernel above carries no trace of it.
+template <int Q, typename S, typename R, int TX, int TY, int NP>
+__global__ void __launch_bounds__(TX* TY + NP) fused_step_fault_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                                                                       KParams<R> p, MarchGeom G, Counters* cnt,
+                                                                       int fault_plane) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fused_tile<Q, S, R, TX, TY, NP, true>(src, dst, &p, G, p.step, blockIdx.x * TX, blockIdx.y * TY,
+                                          blockIdx.z * G.chunk, cnt, smem_raw, fault_plane);
 }
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,7 @@ struct lbm_handle {
     long long steps = 0;
     bool initialised = false;
     bool fused_ready = false;   // shared-memory limit of the fused kernel raised
+    int fault_drop = 0;         // LBM_FAULT_DROP_HANDOFF test hook: 1 + plane, 0 = off
     cudaStream_t stream = nullptr;
 };
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -110,8 +111,8 @@ int sync_and_latch(lbm_handle* h) {
     if (rc) return rc;
     if (c.timeouts) {
         set_error("fused step: a producer/consumer hand-off wait gave up (" + std::to_string(c.timeouts) +
-                  " times); the results of the steps since the last check are not valid");
-        return LBM_ERR_CUDA;
+                  " times); the state is not valid until lbm_init or lbm_set_state");
+        return LBM_ERR_TIMEOUT;
     }
     if (c.bad > h->reported_bad) {
         h->reported_bad = c.bad;
@@ -208,6 +209,13 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
     h->nn = (long long)p->nx * p->ny * p->nz;
     h->elem = p->storage == LBM_STORE_FP64 ? 8 : (p->storage == LBM_STORE_FP32 ? 4 : 2);
     h->stream = (cudaStream_t)p->stream;
+    // fault injection for tests: the fused step's first CTA withholds the
+    // hand-off of this plane, so its consumers' bounded wait runs out
+    if (const char* f = std::getenv("LBM_FAULT_DROP_HANDOFF")) {
+        char* end = nullptr;
+        const long v = std::strtol(f, &end, 10);
+        if (end != f && v >= 0 && v < (1l << 30)) h->fault_drop = (int)v + 1;
+    }
     const size_t popb = (size_t)2 * h->Q * h->nn * h->elem;
     const size_t fldb = (h->Q == 9 ? lbm::Backend<9>::field_bytes(p->storage)
                                    : lbm::Backend<19>::field_bytes(p->storage)) * (size_t)h->nn;
@@ -384,7 +392,7 @@ int lbm_diagnostics(lbm_handle* h, double out[8]) {
         return rc;
     if ((rc = cuda_error(cudaMemcpyAsync(&c, h->cnt, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "diag copy")))
         return rc;
-    if ((rc = sync_and_latch(h)) == LBM_ERR_CUDA) return rc;
+    if ((rc = sync_and_latch(h)) == LBM_ERR_CUDA || rc == LBM_ERR_TIMEOUT) return rc;
     for (int q = 0; q < lbm::kSums; ++q) out[q] = sums[q];
     out[5] = (double)c.clamps;
     out[6] = (double)c.bad;

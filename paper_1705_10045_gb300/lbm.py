@@ -25,6 +25,7 @@ LBM_ERR_UNSTABLE_PARAMS = -2
 LBM_ERR_OOM = -3
 LBM_ERR_CUDA = -4
 LBM_ERR_NONPHYSICAL = -5
+LBM_ERR_TIMEOUT = -6
 
 LBM_D2Q9 = 9
 LBM_D3Q19 = 19

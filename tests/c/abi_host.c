@@ -12,6 +12,8 @@ int main(void) {
     printf("sizeof_params %zu\n", sizeof(lbm_params));
     printf("sizeof_slab %zu\n", sizeof(lbm_slab));
     printf("defaults %d %d %d %d %.17g %.17g %d\n", p.lattice, p.nx, p.ny, p.nz, p.kappa, p.A, p.storage);
+    printf("codes %d %d %d %d %d %d %d\n", LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNSTABLE_PARAMS, LBM_ERR_OOM,
+           LBM_ERR_CUDA, LBM_ERR_NONPHYSICAL, LBM_ERR_TIMEOUT);
 
     double rv = 0.0, rl = 0.0;
     int rc = lbm_coexistence(0.8, &rv, &rl);

@@ -44,6 +44,12 @@ def test_struct_sizes_match_the_python_mirrors(program):
     assert int(program["sizeof_slab"][0]) == ctypes.sizeof(lbm.lbm_slab)
 
 
+def test_error_codes_match_the_python_constants(program):
+    assert [int(v) for v in program["codes"]] == [lbm.LBM_OK, lbm.LBM_ERR_INVALID_ARG, lbm.LBM_ERR_UNSTABLE_PARAMS,
+                                                  lbm.LBM_ERR_OOM, lbm.LBM_ERR_CUDA, lbm.LBM_ERR_NONPHYSICAL,
+                                                  lbm.LBM_ERR_TIMEOUT]
+
+
 def test_host_calls_from_c(program):
     assert program["defaults"] == ["9", "64", "64", "1", "0.01", "-0.152", str(lbm.LBM_STORE_FP32)]
     rc, rv, rl = program["coexistence"]

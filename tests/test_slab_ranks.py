@@ -102,10 +102,8 @@ def _rank(rank, world, port, case, out, leave_after):
             except RuntimeError as e:
                 out[rank] = ("failed", s, str(e)[:200])
                 return
-        own = slice(slab.lo, slab.lo + slab.own)
         out[rank] = (slab.first, slab.own, _plane_view(st.N, Q, slab.lo, slab.own).copy(),
                      _plane_view(st.g, Q, slab.lo, slab.own).copy())
-        del own
     finally:
         if leave_after is None:
             dist.destroy_process_group()

@@ -5,8 +5,9 @@ put back together, must equal the undivided oracle run bit for bit: this
 checks the halo depth (three planes per cut), the neighbour and tag pairing
 of the swap, the periodic wrap and the treatment of the cut ends (fixed wall
 temperatures only at the domain's walls) independently of the GPU.  A rank
-that leaves between steps makes its neighbour's next swap fail instead of
-hanging."""
+that leaves between steps, or stays but withholds its halo, makes its
+neighbour's swap fail (at once, or after the process group's timeout)
+instead of hanging."""
 import datetime
 import os
 import socket
@@ -61,7 +62,7 @@ def _plane_view(a, Q, first, count):
     return a[:, first:first + count] if Q == 19 else a[:, :, first:first + count]
 
 
-def _rank(rank, world, port, case, out, leave_after):
+def _rank(rank, world, port, case, out, leave_after, withhold_at=None, timeout_s=20):
     sys.path.insert(0, ROOT)
     import torch
     import torch.distributed as dist
@@ -71,7 +72,7 @@ def _rank(rank, world, port, case, out, leave_after):
     from paper_1705_10045_gb300.slabs import exchange_halos, local_planes
 
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
-    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=timeout_s))
     try:
         cfg = CASES[case]
         whole = lbm.make_params(**cfg["p"])
@@ -96,6 +97,10 @@ def _rank(rank, world, port, case, out, leave_after):
             if leave_after is not None and rank == world - 1 and s == leave_after:
                 out[rank] = "left"
                 return          # leaves between steps: the process exits, its sockets close
+            if withhold_at is not None and rank == world - 1 and s == withhold_at:
+                time.sleep(timeout_s + 2)   # alive, but its halo never comes
+                out[rank] = "withheld"
+                return
             st.step(1)
             try:
                 exchange_halos(dist, slab, get, put)
@@ -105,7 +110,7 @@ def _rank(rank, world, port, case, out, leave_after):
         out[rank] = (slab.first, slab.own, _plane_view(st.N, Q, slab.lo, slab.own).copy(),
                      _plane_view(st.g, Q, slab.lo, slab.own).copy())
     finally:
-        if leave_after is None:
+        if leave_after is None and withhold_at is None:
             dist.destroy_process_group()
 
 
@@ -146,4 +151,19 @@ def test_a_rank_that_leaves_makes_its_neighbours_swap_fail_not_hang():
     assert got[1] == "left"
     status, step, _ = got[0]
     assert status == "failed" and step == leave_after
+    assert time.monotonic() - t0 < 60
+
+
+def test_a_rank_that_withholds_its_halo_makes_the_swap_time_out():
+    world, at, timeout_s = 2, 4, 3
+    t0 = time.monotonic()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, _free_port(), "d2q9_periodic_2", out, None, at, timeout_s), nprocs=world,
+                 join=True)
+        got = dict(out)
+    assert got[1] == "withheld"
+    status, step, msg = got[0]
+    assert status == "failed" and step == at
+    assert "Timed out" in msg or "timeout" in msg.lower()
     assert time.monotonic() - t0 < 60

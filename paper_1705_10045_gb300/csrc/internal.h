@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include <nvtx3/nvToolsExt.h>
 
 struct lbm_handle {
     lbm_params p;
@@ -51,6 +52,15 @@ struct lbm_batch {
 namespace lbm {
 
 constexpr int kGraphLaunches = 32;
+
+// NVTX range around a library call: named spans on a profiler's timeline
+// (Nsight Systems), a cheap no-op when no tool is attached.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // error reporting shared by the translation units
 void set_error(const std::string& msg);

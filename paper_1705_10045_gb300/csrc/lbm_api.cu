@@ -150,6 +150,7 @@ void lbm_default_params(lbm_params* p) {
 }
 
 int lbm_create(const lbm_params* p, lbm_handle** out) {
+    lbm::TraceRange trace_("lbm_create");
     if (!p || !out) {
         set_error("lbm_create: null argument");
         return LBM_ERR_INVALID_ARG;
@@ -245,6 +246,7 @@ int lbm_coexistence(double T, double* rho_v, double* rho_l) {
 }
 
 int lbm_init(lbm_handle* h, const double* rho, const double* u, const double* eps, int mem) {
+    lbm::TraceRange trace_("lbm_init");
     if (int rc = check_handle(h)) return rc;
     if (!rho || !u || !eps || (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE)) {
         set_error("lbm_init: null field or bad mem flag");
@@ -292,6 +294,7 @@ int lbm_init(lbm_handle* h, const double* rho, const double* u, const double* ep
 }
 
 int lbm_step(lbm_handle* h, int n) {
+    lbm::TraceRange trace_("lbm_step");
     if (int rc = check_handle(h)) return rc;
     if (int rc = need_init(h)) return rc;
     if (n < 0) {
@@ -306,6 +309,7 @@ int lbm_step(lbm_handle* h, int n) {
 }
 
 int lbm_moments(lbm_handle* h, double* rho, double* u, double* T, double* P, int mem) {
+    lbm::TraceRange trace_("lbm_moments");
     if (int rc = check_handle(h)) return rc;
     if (int rc = need_init(h)) return rc;
     if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) {
@@ -337,6 +341,7 @@ int lbm_moments(lbm_handle* h, double* rho, double* u, double* T, double* P, int
 }
 
 int lbm_moments_f(lbm_handle* h, float* rho, float* u, float* T, float* P, int mem) {
+    lbm::TraceRange trace_("lbm_moments_f");
     if (int rc = check_handle(h)) return rc;
     if (int rc = need_init(h)) return rc;
     if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) {
@@ -376,6 +381,7 @@ int lbm_moments_f(lbm_handle* h, float* rho, float* u, float* T, float* P, int m
 }
 
 int lbm_diagnostics(lbm_handle* h, double out[8]) {
+    lbm::TraceRange trace_("lbm_diagnostics");
     if (int rc = check_handle(h)) return rc;
     if (int rc = need_init(h)) return rc;
     if (!out) {
@@ -406,6 +412,7 @@ size_t lbm_state_bytes(const lbm_handle* h) {
 }
 
 int lbm_get_state(lbm_handle* h, void* buf, int mem) {
+    lbm::TraceRange trace_("lbm_get_state");
     if (int rc = check_handle(h)) return rc;
     if (int rc = need_init(h)) return rc;
     if (!buf || (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE)) {
@@ -433,6 +440,7 @@ int lbm_get_state(lbm_handle* h, void* buf, int mem) {
 }
 
 int lbm_set_state(lbm_handle* h, const void* buf, int mem) {
+    lbm::TraceRange trace_("lbm_set_state");
     if (int rc = check_handle(h)) return rc;
     if (!buf || (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE)) {
         set_error("lbm_set_state: null buffer or bad mem flag");
@@ -471,6 +479,7 @@ int lbm_set_state(lbm_handle* h, const void* buf, int mem) {
 }
 
 int lbm_sync(lbm_handle* h) {
+    lbm::TraceRange trace_("lbm_sync");
     if (int rc = check_handle(h)) return rc;
     DeviceGuard dg(h->p.device);
     return sync_and_latch(h);
@@ -482,6 +491,7 @@ int lbm_launches_per_step(const lbm_handle* h) {
 }
 
 int lbm_profile_step(lbm_handle* h, int n, double* ms, int cap) {
+    lbm::TraceRange trace_("lbm_profile_step");
     if (int rc = check_handle(h)) return rc;
     if (int rc = need_init(h)) return rc;
     if (n < 1 || !ms || cap < 1) {

@@ -189,6 +189,7 @@ int lbm_batch_create(const lbm_params* common, lbm_batch** out) {
 
 int lbm_batch_add(lbm_batch* b, const lbm_params* p, const double* rho, const double* u, const double* eps, int mem,
                   long long steps, int* id) {
+    lbm::TraceRange trace_("lbm_batch_add");
     if (int rc = check_batch(b)) return rc;
     if (!p || !id || steps < 0) {
         set_error("lbm_batch_add: null parameters or id, or steps < 0");
@@ -233,6 +234,7 @@ int lbm_batch_remove(lbm_batch* b, int id) {
 }
 
 int lbm_batch_step(lbm_batch* b, int n) {
+    lbm::TraceRange trace_("lbm_batch_step");
     if (int rc = check_batch(b)) return rc;
     if (n < 0) {
         set_error("lbm_batch_step: n < 0");
@@ -321,6 +323,7 @@ int lbm_batch_set_variant(lbm_batch* b, int v) {
 }
 
 int lbm_batch_tune(lbm_batch* b, int reps, int* best, double* ms) {
+    lbm::TraceRange trace_("lbm_batch_tune");
     if (int rc = check_batch(b)) return rc;
     if (reps < 1) {
         set_error("lbm_batch_tune: reps < 1");
@@ -373,6 +376,7 @@ int lbm_batch_tune(lbm_batch* b, int reps, int* best, double* ms) {
 }
 
 int lbm_batch_sync(lbm_batch* b) {
+    lbm::TraceRange trace_("lbm_batch_sync");
     if (int rc = check_batch(b)) return rc;
     int rc = LBM_OK;
     for (auto* h : b->doms)

@@ -329,6 +329,7 @@ lbm_handle* lbm_slabs_domain(lbm_slabs* s, int i) {
 }
 
 int lbm_slabs_init(lbm_slabs* s, const double* rho, const double* u, const double* eps, int mem) {
+    lbm::TraceRange trace_("lbm_slabs_init");
     if (int rc = check_slabs(s)) return rc;
     if (!rho || !u || !eps || (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE)) {
         set_error("lbm_slabs_init: null field or bad mem flag");
@@ -364,6 +365,7 @@ int lbm_slabs_init(lbm_slabs* s, const double* rho, const double* u, const doubl
 }
 
 int lbm_slabs_step(lbm_slabs* s, int n) {
+    lbm::TraceRange trace_("lbm_slabs_step");
     if (int rc = check_slabs(s)) return rc;
     if (n < 0) {
         set_error("lbm_slabs_step: n < 0");
@@ -373,6 +375,7 @@ int lbm_slabs_step(lbm_slabs* s, int n) {
     for (int t = 0; t < n; ++t) {
         for (int i = 0; i < s->count; ++i)
             if (int rc = lbm_step(s->h[i], 1)) return rc;
+        lbm::TraceRange swap_("halo swap");
         if (int rc = exchange(s)) return rc;
         ++s->steps;
     }
@@ -380,6 +383,7 @@ int lbm_slabs_step(lbm_slabs* s, int n) {
 }
 
 int lbm_slabs_moments(lbm_slabs* s, double* rho, double* u, double* T, double* P, int mem) {
+    lbm::TraceRange trace_("lbm_slabs_moments");
     if (int rc = check_slabs(s)) return rc;
     if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) {
         set_error("lbm_slabs_moments: bad mem flag");
@@ -418,6 +422,7 @@ int lbm_slabs_moments(lbm_slabs* s, double* rho, double* u, double* T, double* P
 }
 
 int lbm_slabs_diagnostics(lbm_slabs* s, double out[8]) {
+    lbm::TraceRange trace_("lbm_slabs_diagnostics");
     if (int rc = check_slabs(s)) return rc;
     if (!out) {
         set_error("lbm_slabs_diagnostics: null output");

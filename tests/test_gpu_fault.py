@@ -5,7 +5,9 @@ makes one wait run out through the library's fault-injection hook
 (LBM_FAULT_DROP_HANDOFF: the first CTA withholds one plane's hand-off) and
 checks that the host gets LBM_ERR_TIMEOUT, that the error stays latched until
 the handle gets a new state, and that the device context stays usable: a
-handle created afterwards steps bit for bit like a fresh one."""
+handle created afterwards steps bit for bit like a fresh one.  A domain
+larger than device memory is refused with LBM_ERR_OOM (its first allocation
+already fails, so nothing is held) and leaves the device usable."""
 import time
 
 import numpy as np
@@ -58,3 +60,20 @@ def test_a_withheld_hand_off_times_out_and_is_reported(monkeypatch, storage):
     finally:
         a.close()
         b.close()
+
+
+def test_a_domain_larger_than_device_memory_is_refused_cleanly():
+    import torch
+    # 2048 x 1024 x 1023 nodes (just under the 2^31-node limit) in FP64: the
+    # first population buffer alone would be 2 Q 8 B = 304 B x 2.1e9 = 652 GB
+    p = lbm.make_params(lattice=19, nx=2048, ny=1024, nz=1023, storage=lbm.LBM_STORE_FP64)
+    assert lbm.lbm_domain_bytes(p) > torch.cuda.get_device_properties(0).total_memory
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(p)
+    assert e.value.code == lbm.LBM_ERR_OOM
+    sim, _ = _sim()
+    try:
+        sim.step(2)
+        assert sim.diagnostics()["bad"] == 0
+    finally:
+        sim.close()

@@ -22,6 +22,10 @@ void set_error(const std::string& msg) { g_error = msg; }
 
 int cuda_error(cudaError_t e, const char* where) {
     if (e == cudaSuccess) return LBM_OK;
+    // the runtime also keeps the error as its last error; clear it so that a
+    // later launch check does not report it again (a failed allocation is not
+    // sticky and leaves the context usable)
+    (void)cudaGetLastError();
     set_error(std::string(where) + ": " + cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
 }

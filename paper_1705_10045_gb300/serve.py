@@ -11,6 +11,13 @@ memory is freed for the next arrivals.  Admission is first come, first
 served: a job that does not fit blocks later arrivals (no reordering), so
 large jobs are not starved.
 
+A failing job fails alone.  A job larger than the whole memory budget is
+rejected on arrival.  The library may refuse a job when it is added (bad
+parameters, a non-physical or unstable initial state, no device memory).
+Or its state may turn non-physical while it runs, which shows when its
+results are read.  In each case the job gets an ``error`` and no result,
+its slot and memory are freed, and the other jobs go on.
+
 Which resident jobs advance in a round is the policy's choice:
 
 * ``"fill"`` (default): jobs in admission order, the oldest first, are
@@ -49,6 +56,7 @@ class Job:
     admitted: Optional[float] = None
     completed: Optional[float] = None
     result: Optional[dict] = None
+    error: Optional[str] = None                # why the job failed (None: it succeeded)
 
     @property
     def latency(self) -> Optional[float]:
@@ -67,6 +75,7 @@ class ServeStats:
     lattice_updates: float
     mlups: float
     extra: dict = field(default_factory=dict)
+    failed: int = 0
 
 
 def _percentile(xs, q):
@@ -74,11 +83,12 @@ def _percentile(xs, q):
 
 
 def _stats(jobs, wall, max_resident, peak_bytes, lu) -> ServeStats:
-    lat = [j.latency for j in jobs if j.latency is not None]
+    lat = [j.latency for j in jobs if j.latency is not None and j.error is None]
     done = len(lat)
     return ServeStats(completed=done, wall_s=wall, jobs_per_s=done / wall if wall > 0 else float("nan"),
                       p50_s=_percentile(lat, 50), p99_s=_percentile(lat, 99), max_resident=max_resident,
-                      peak_bytes=peak_bytes, lattice_updates=lu, mlups=lu / wall / 1e6 if wall > 0 else float("nan"))
+                      peak_bytes=peak_bytes, lattice_updates=lu, mlups=lu / wall / 1e6 if wall > 0 else float("nan"),
+                      failed=sum(1 for j in jobs if j.error is not None))
 
 
 def _nodes(params: dict) -> int:
@@ -111,26 +121,39 @@ class Server:
         kw = dict(job.params, lattice=self.lattice, storage=self.storage)
         return lbm.lbm_domain_bytes(lbm.make_params(**kw))
 
-    def _admit(self, job: Job, now: float) -> None:
+    @staticmethod
+    def _fail(job: Job, why: str, now: float) -> None:
+        job.error = why
+        job.completed = now
+
+    def _admit(self, job: Job, nbytes: int, now: float) -> bool:
         rho, u, T = job.fields()
         kw = dict(job.params)
         c_v = kw.get("c_v", 1.5)
         d = 2 if self.lattice == lbm.LBM_D2Q9 else 3
-        slot = self.batch.add(np.ascontiguousarray(rho), np.ascontiguousarray(u[:d]), np.ascontiguousarray(c_v * T),
-                              job.steps, **kw)
-        nbytes = self.job_bytes(job)
+        try:
+            slot = self.batch.add(np.ascontiguousarray(rho), np.ascontiguousarray(u[:d]),
+                                  np.ascontiguousarray(c_v * T), job.steps, **kw)
+        except lbm.LbmError as e:
+            self._fail(job, str(e), now)
+            return False
         self.resident[slot] = (job, nbytes)
         self.bytes_in_use += nbytes
         job.admitted = now
+        return True
 
     def _retire(self, slot: int, now_fn) -> None:
         job, nbytes = self.resident.pop(slot)
-        res = self.batch.moments(slot)
-        res["diagnostics"] = self.batch.diagnostics(slot)
-        job.result = res if self.keep_fields else {"diagnostics": res["diagnostics"]}
-        self.batch.remove(slot)
-        self.bytes_in_use -= nbytes
-        job.completed = now_fn()
+        try:
+            res = self.batch.moments(slot)
+            res["diagnostics"] = self.batch.diagnostics(slot)
+            job.result = res if self.keep_fields else {"diagnostics": res["diagnostics"]}
+        except lbm.LbmError as e:      # e.g. its state turned non-physical
+            job.error = str(e)
+        finally:
+            self.batch.remove(slot)
+            self.bytes_in_use -= nbytes
+            job.completed = now_fn()
 
     def run(self, jobs: list, clock: Callable[[], float] = time.perf_counter) -> ServeStats:
         """Serve a trace: jobs become available at their arrival times
@@ -145,20 +168,29 @@ class Server:
             t = now()
             # admit arrivals in order while memory and slots allow (head-of-line blocking)
             while nxt < len(queue) and queue[nxt].arrival <= t and len(self.resident) < self.max_slots:
-                need = self.job_bytes(queue[nxt])
+                job = queue[nxt]
+                try:
+                    need = self.job_bytes(job)
+                except (lbm.LbmError, AttributeError, ValueError, TypeError) as e:
+                    self._fail(job, f"bad parameters: {e}", t)
+                    nxt += 1
+                    continue
+                if need > self.memory_budget:
+                    self._fail(job, f"needs {need} bytes of device memory, the budget is {self.memory_budget}", t)
+                    nxt += 1
+                    continue
                 if self.resident and self.bytes_in_use + need > self.memory_budget:
                     break
-                if need > self.memory_budget:
-                    raise MemoryError(f"job {queue[nxt].name} needs {need} bytes, budget {self.memory_budget}")
-                self._admit(queue[nxt], t)
+                self._admit(job, need, t)
                 nxt += 1
             max_resident = max(max_resident, len(self.resident))
             peak = max(peak, self.bytes_in_use)
             if not self.resident:
                 # idle until the next arrival
-                wait = queue[nxt].arrival - now()
-                if wait > 0:
-                    time.sleep(wait)
+                if nxt < len(queue):
+                    wait = queue[nxt].arrival - now()
+                    if wait > 0:
+                        time.sleep(wait)
                 continue
             # advance the chosen jobs by the quantum (each stops at its own budget);
             # a shorter quantum when a job is about to finish keeps its latency low
@@ -210,18 +242,22 @@ def run_sequential(jobs: list, lattice: int, storage: int, device: int = 0, keep
         job.admitted = now()
         rho, u, T = job.fields()
         kw = dict(job.params)
-        sim = lbm.Lbm(lattice=lattice, storage=storage, device=device, **kw)
+        sim = None
         try:
+            sim = lbm.Lbm(lattice=lattice, storage=storage, device=device, **kw)
             c_v = kw.get("c_v", 1.5)
             sim.init(np.ascontiguousarray(rho), np.ascontiguousarray(u[: sim.d]), np.ascontiguousarray(c_v * T))
             sim.step(job.steps)
             res = sim.moments()
             res["diagnostics"] = lbm.lbm_diagnostics(sim.h)
+            job.result = res if keep_fields else {"diagnostics": res["diagnostics"]}
+            lu += job.steps * _nodes(job.params)
+        except lbm.LbmError as e:
+            job.error = str(e)
         finally:
-            sim.close()
-        job.result = res if keep_fields else {"diagnostics": res["diagnostics"]}
+            if sim is not None:
+                sim.close()
         job.completed = now()
-        lu += job.steps * _nodes(job.params)
     return _stats(queue, now(), 1, 0, lu)
 
 

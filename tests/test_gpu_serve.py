@@ -77,3 +77,40 @@ def test_late_arrivals_wait_and_sequential_baseline_matches():
     assert st2.completed == 3
     for a, b in zip(jobs, seq):
         assert np.array_equal(a.result["rho"], b.result["rho"])
+
+
+def test_a_failing_job_fails_alone():
+    """A job whose initial density is not positive is refused when it is
+    added, and one larger than the budget is rejected on arrival; both get an
+    error and free nothing they did not take, and the other jobs' results
+    are the ones they get alone."""
+    jobs = _small_trace(count=6, seed=13)
+    bad_fields = jobs[1].fields
+
+    def negative_density():
+        rho, u, T = bad_fields()
+        rho = rho.copy()
+        rho.flat[7] = -0.1
+        return rho, u, T
+
+    jobs[1].fields = negative_density
+    per_job = max(lbm.lbm_domain_bytes(lbm.make_params(lattice=19, storage=lbm.LBM_STORE_FP32, **j.params))
+                  for j in jobs)
+    budget = 3 * per_job
+    jobs[3].params = dict(jobs[3].params, nx=256, ny=256, nz=256)   # far over the budget
+    srv = serve.Server(lbm.LBM_D3Q19, lbm.LBM_STORE_FP32, memory_budget=budget, quantum=16)
+    try:
+        st = srv.run(jobs)
+        assert not srv.resident and srv.bytes_in_use == 0 and srv.batch.size() == 0
+    finally:
+        srv.close()
+    assert st.failed == 2 and st.completed == len(jobs) - 2
+    assert jobs[1].error and "lbm_init" in jobs[1].error and jobs[1].result is None
+    assert jobs[3].error and "budget" in jobs[3].error and jobs[3].result is None
+    for k, j in enumerate(jobs):
+        if k in (1, 3):
+            continue
+        assert j.error is None
+        alone = _alone(j)
+        for f in ("rho", "u", "T", "P"):
+            assert np.array_equal(j.result[f], alone[f]), (j.name, f)

@@ -234,14 +234,15 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         const int nm = G.nm;
         const R third = R(1.0 / 3.0);
         // the node's g populations first: their loads are in flight while the
-        // finite differences below read shared memory
+        // finite differences below read shared memory.  The reload is the last
+        // use of these lines on this SM, so it does not allocate them in L1.
         const int n = c * plane_n + n_ab;
         R hv[Q];
         {
             const S* qg = src + n + (size_t)Q * nn;
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
-                hv[k] = Store<S, R>::load(qg, 0, R(V::w(k)) * p->E_ref);
+                hv[k] = Store<S, R>::load_last(qg, 0, R(V::w(k)) * p->E_ref);
                 qg += nn;
             }
         }
@@ -344,7 +345,7 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
             };
             {
                 const R w0 = R(V::w(0));
-                emit(0, w0 * base0, w0 * dbase, Store<S, R>::load(qn, 0, w0 * p->rho_ref), hv[0]);
+                emit(0, w0 * base0, w0 * dbase, Store<S, R>::load_last(qn, 0, w0 * p->rho_ref), hv[0]);
                 qn += nn;
             }
 #pragma unroll
@@ -356,8 +357,8 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
                 if (M::m(k) == 1) { cu += u[2]; cd += dv[2]; } else if (M::m(k) == -1) { cu -= u[2]; cd -= dv[2]; }
                 const R ev = wk * fma(R(4.5) * cu, cu, base0), od = (R(3) * wk) * cu;
                 const R dv_e = wk * fma(R(4.5) * cd, fma(R(2), cu, cd), dbase), dv_o = (R(3) * wk) * cd;
-                const R fa = Store<S, R>::load(qn, 0, wk * p->rho_ref);
-                const R fb = Store<S, R>::load(qn + nn, 0, wk * p->rho_ref);
+                const R fa = Store<S, R>::load_last(qn, 0, wk * p->rho_ref);
+                const R fb = Store<S, R>::load_last(qn + nn, 0, wk * p->rho_ref);
                 qn += 2 * nn;
                 emit(k, ev + od, dv_e + dv_o, fa, hv[k]);
                 emit(k + 1, ev - od, dv_e - dv_o, fb, hv[k + 1]);

@@ -92,16 +92,29 @@ __device__ __forceinline__ unsigned slot_bits(unsigned nb, int slot) {
 }
 
 template <typename S, typename R> struct Store;
+// load_last: the same load for the last use of a value on this SM (the fused
+// step's consumer reload); L1::no_allocate leaves L1 to the lines the moment
+// stage will still reuse.
 
 template <> struct Store<double, double> {
     static constexpr bool kStochastic = false;
     __device__ static double load(const double* p, size_t i, double) { return p[i]; }
+    __device__ static double load_last(const double* p, size_t i, double) {
+        double v;
+        asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p + i));
+        return v;
+    }
     __device__ static void store(double* p, size_t i, double v, double, unsigned = 0) { p[i] = v; }
 };
 
 template <> struct Store<float, float> {
     static constexpr bool kStochastic = false;
     __device__ static float load(const float* p, size_t i, float) { return __ldg(p + i); }
+    __device__ static float load_last(const float* p, size_t i, float) {
+        float v;
+        asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p + i));
+        return v;
+    }
     __device__ static void store(float* p, size_t i, float v, float, unsigned = 0) { p[i] = v; }
 };
 
@@ -109,6 +122,11 @@ template <> struct Store<__half, float> {
     static constexpr bool kStochastic = true;
     __device__ static float load(const __half* p, size_t i, float shift) {
         return __half2float(__ldg(p + i)) + shift;
+    }
+    __device__ static float load_last(const __half* p, size_t i, float shift) {
+        unsigned short b;
+        asm("ld.global.nc.L1::no_allocate.b16 %0, [%1];" : "=h"(b) : "l"(p + i));
+        return __half2float(__ushort_as_half(b)) + shift;
     }
     // rnd13: 13 random bits; adding them below the 10 FP16 mantissa bits of
     // the FP32 value and truncating rounds the magnitude up with probability

@@ -29,6 +29,8 @@ CASES = {
     # D3Q19 walls with a heated floor, variable conductivity
     "d3q19_walls_2": dict(world=2, steps=12, p=dict(lattice=19, nx=8, ny=6, nz=16, wall=1, T_fixed_lo=1,
                                                    T_lo=0.85, chi_mode=1, chi=0.05)),
+    # D3Q19 periodic in three slabs of 6, 6 and 5 planes: the first slab's lower halo wraps to the top
+    "d3q19_periodic_3": dict(world=3, steps=10, p=dict(lattice=19, nx=6, ny=6, nz=17, latent=0.02)),
 }
 
 

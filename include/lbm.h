@@ -310,6 +310,8 @@ typedef struct lbm_slabs lbm_slabs;
  * and a field buffer of (d + 3) planes of doubles per node of the largest
  * slab.  Errors as lbm_slab_plan and lbm_create. */
 int lbm_slabs_create(const lbm_params* p, int count, lbm_slabs** out);
+
+/* Number of slabs (LBM_ERR_INVALID_ARG for NULL). */
 int lbm_slabs_count(const lbm_slabs* s);
 
 /* Handle of slab i (owned by the slabs object; NULL if out of range). */
@@ -335,6 +337,8 @@ int lbm_slabs_diagnostics(lbm_slabs* s, double out[8]);
 
 /* Wait for every slab; returns a latched device error if any. */
 int lbm_slabs_sync(lbm_slabs* s);
+
+/* Free every slab handle and the field buffer.  NULL is allowed. */
 void lbm_slabs_destroy(lbm_slabs* s);
 
 /* Halo exchange between processes (one slab handle per process): bytes of one

@@ -51,6 +51,9 @@ class _Params(ctypes.Structure):
         ("g", ctypes.c_double * 3),
         ("wall", ctypes.c_int), ("T_fixed_lo", ctypes.c_int), ("T_fixed_hi", ctypes.c_int),
         ("T_lo", ctypes.c_double), ("T_hi", ctypes.c_double),
+        ("wall_x", ctypes.c_int), ("wall_y", ctypes.c_int),
+        ("T_fixed_x", ctypes.c_int * 2), ("T_fixed_y", ctypes.c_int * 2),
+        ("T_x", ctypes.c_double * 2), ("T_y", ctypes.c_double * 2),
         ("pressure_work", ctypes.c_int), ("conduction", ctypes.c_int), ("pseudoforce", ctypes.c_int),
         ("latent", ctypes.c_double), ("coex", ctypes.POINTER(ctypes.c_double)),
     ]
@@ -79,6 +82,12 @@ class Params:
     T_fixed_hi: bool = False
     T_lo: float = 0.0
     T_hi: float = 0.0
+    wall_x: bool = False          # bounce-back walls at both ends of x
+    wall_y: bool = False          # ... of y (D3Q19; for D2Q9 y is the last axis, `wall`)
+    T_fixed_x: tuple = (False, False)   # per x wall (low, high end): held at T_x[i]
+    T_fixed_y: tuple = (False, False)
+    T_x: tuple = (0.0, 0.0)
+    T_y: tuple = (0.0, 0.0)
     pressure_work: bool = True
     conduction: bool = True
     pseudoforce: bool = True
@@ -93,10 +102,16 @@ class Params:
         return (self.nz, self.ny, self.nx)
 
     def to_c(self) -> _Params:
+        if self.Q == 9 and self.wall_y:
+            raise ValueError("D2Q9: y is the last axis; its walls are `wall`")
         c = _Params()
         for name, _ in _Params._fields_:
             if name == "g":
                 c.g = (ctypes.c_double * 3)(*[float(v) for v in self.g])
+            elif name in ("T_fixed_x", "T_fixed_y"):
+                setattr(c, name, (ctypes.c_int * 2)(*[int(v) for v in getattr(self, name)]))
+            elif name in ("T_x", "T_y"):
+                setattr(c, name, (ctypes.c_double * 2)(*[float(v) for v in getattr(self, name)]))
             elif name == "coex":
                 c.coex = _ptr(coexistence_table())
             else:

@@ -39,6 +39,10 @@ typedef struct {
     int wall;            /* last axis: 0 periodic, 1 bounce-back walls at both ends */
     int T_fixed_lo, T_fixed_hi;   /* wall temperature mode: 0 adiabatic, 1 fixed */
     double T_lo, T_hi;
+    int wall_x;          /* x axis: 0 periodic, 1 bounce-back walls at both ends */
+    int wall_y;          /* y axis of D3Q19 (for D2Q9 y is the last axis: `wall`) */
+    int T_fixed_x[2], T_fixed_y[2];   /* per wall (low, high end): 0 adiabatic, 1 fixed */
+    double T_x[2], T_y[2];
     int pressure_work, conduction, pseudoforce;   /* physics switches */
     double latent;       /* rho_liq Q of Sec. 5 (energy per volume); 0: no latent heat */
     const double* coex;  /* Maxwell densities on the temperature grid below:
@@ -133,42 +137,60 @@ double orc_pressure(const orc_params* p, double rho, double T)
 }
 
 /* ---------------------------------------------------------------------- */
-/* Neighbour lookup.  x and y (for D3Q19) are periodic.  The last axis is
- * periodic or closed by walls half a node outside the first and last
- * layer.  Outside a wall, the stencils read the mirror node (a node at
- * distance m beyond the wall mirrors the node at distance m-1 inside). */
+/* Neighbour lookup.  Each axis is periodic or closed by walls half a node
+ * outside its first and last layer (the last axis through `wall`, x through
+ * `wall_x`, y of D3Q19 through `wall_y`).  Outside a wall the stencils read
+ * the mirror node (a node at distance m beyond the wall mirrors the node at
+ * distance m-1 inside); g[a] is -1 / +1 when the step crosses the low / high
+ * wall of axis a, and ghost is nonzero when it crosses any wall. */
 
-typedef struct { long n; int ghost; } nb_t;
+typedef struct { long n; int ghost; int g[3]; } nb_t;
 
 static int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
+
+/* coordinate i + d along an axis of n nodes, periodic or walled */
+static int axis_step(int i, int n, int walled, int* g)
+{
+    *g = 0;
+    if (!walled) return wrap(i, n);
+    if (i < 0) { *g = -1; return -1 - i; }
+    if (i >= n) { *g = 1; return 2 * n - 1 - i; }
+    return i;
+}
 
 static nb_t neighbour(const orc_params* p, int x, int y, int z, int dx, int dy, int dz)
 {
     nb_t r;
-    r.ghost = 0;
-    int X = wrap(x + dx, p->nx);
+    int X = axis_step(x + dx, p->nx, p->wall_x, &r.g[0]);
     int Y, Z;
     if (p->Q == 9) {
+        Y = axis_step(y + dy, p->ny, p->wall, &r.g[1]);
         Z = 0;
-        Y = y + dy;
-        if (p->wall) {
-            if (Y < 0) { Y = -1 - Y; r.ghost = -1; }
-            else if (Y >= p->ny) { Y = 2 * p->ny - 1 - Y; r.ghost = 1; }
-        } else {
-            Y = wrap(Y, p->ny);
-        }
+        r.g[2] = 0;
     } else {
-        Y = wrap(y + dy, p->ny);
-        Z = z + dz;
-        if (p->wall) {
-            if (Z < 0) { Z = -1 - Z; r.ghost = -1; }
-            else if (Z >= p->nz) { Z = 2 * p->nz - 1 - Z; r.ghost = 1; }
-        } else {
-            Z = wrap(Z, p->nz);
-        }
+        Y = axis_step(y + dy, p->ny, p->wall_y, &r.g[1]);
+        Z = axis_step(z + dz, p->nz, p->wall, &r.g[2]);
     }
+    r.ghost = r.g[0] != 0 || r.g[1] != 0 || r.g[2] != 0;
     r.n = ((long)Z * p->ny + Y) * p->nx + X;
     return r;
+}
+
+/* Temperature mode of the wall at end `hi` (0 low, 1 high) of axis a:
+ * returns 1 and the wall temperature when that wall is held at a fixed T. */
+static int wall_T(const orc_params* p, int a, int hi, double* Tw)
+{
+    const int last = p->Q == 9 ? 1 : 2;
+    if (a == last) {
+        *Tw = hi ? p->T_hi : p->T_lo;
+        return hi ? p->T_fixed_hi : p->T_fixed_lo;
+    }
+    if (a == 0) {
+        *Tw = p->T_x[hi];
+        return p->T_fixed_x[hi];
+    }
+    *Tw = p->T_y[hi];
+    return p->T_fixed_y[hi];
 }
 
 static long nnodes(const orc_params* p) { return (long)p->nx * p->ny * p->nz; }
@@ -270,8 +292,10 @@ static int coexistence_at(const orc_params* p, double T, double* rv, double* rl)
  *   applied along every axis;
  *   conduction     div(lambda grad T) dt, conservative form with the face
  *   conductivity the mean of the two nodes.
- * Across a wall: u*(ghost) = -u*(mirror) (no-slip), T(ghost) = T(mirror)
- * for an adiabatic wall and 2 T_w - T(mirror) for a wall held at T_w.
+ * Across a wall of axis a: u*_a(ghost) = -u*_a(mirror) (no-slip; only the
+ * component normal to the wall enters the difference along a),
+ * T(ghost) = T(mirror) for an adiabatic wall and 2 T_w - T(mirror) for a wall
+ * held at T_w.
  * Latent heat of the phase transition (Sec. 5), when p->latent = rho_liq Q
  * is nonzero: inside the transition layer rho_v(T) < rho < rho_l(T) the
  * energy changes by  (rho_liq Q / (rho_l - rho_v)) d(rho)/dt  with
@@ -292,13 +316,13 @@ void orc_energy_source(const orc_params* p, const double* rho, const double* ust
                     e[a] = 1;
                     nb_t up = neighbour(p, x, y, z, e[0], e[1], e[2]);
                     nb_t dn = neighbour(p, x, y, z, -e[0], -e[1], -e[2]);
-                    double uu = up.ghost ? -ustar[a * nn + up.n] : ustar[a * nn + up.n];
-                    double ud = dn.ghost ? -ustar[a * nn + dn.n] : ustar[a * nn + dn.n];
+                    double uu = up.g[a] ? -ustar[a * nn + up.n] : ustar[a * nn + up.n];
+                    double ud = dn.g[a] ? -ustar[a * nn + dn.n] : ustar[a * nn + dn.n];
                     div += (uu - ud) / 2.0;
 
-                    double Tu = T[up.n], Td = T[dn.n];
-                    if (up.ghost && p->T_fixed_hi) Tu = 2.0 * p->T_hi - T[up.n];
-                    if (dn.ghost && p->T_fixed_lo) Td = 2.0 * p->T_lo - T[dn.n];
+                    double Tu = T[up.n], Td = T[dn.n], Tw;
+                    if (up.g[a] && wall_T(p, a, 1, &Tw)) Tu = 2.0 * Tw - T[up.n];
+                    if (dn.g[a] && wall_T(p, a, 0, &Tw)) Td = 2.0 * Tw - T[dn.n];
                     double lc = conductivity(p, rho[n]);
                     double lu = (lc + conductivity(p, rho[up.n])) / 2.0;
                     double ld = (lc + conductivity(p, rho[dn.n])) / 2.0;

@@ -7,11 +7,16 @@ liquid layer 64 nodes deep at T = 0.8 under its saturated vapour, gravity
 one lattice update of every node (moments, EOS, force, finite-difference
 energy change, collision of both population sets, streaming, walls).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--mode slabs|replicas]
 
-Prints one JSON line (rank 0).  value = MLUPS over all ranks (each rank runs
-its own replica of the workload: weak scaling).  The populations (11.5 GB of
-reads and writes per step) are far larger than L2, so no flush is needed.
+Prints one JSON line (rank 0).  With one GPU the workload runs undivided.
+With N > 1 ranks (torchrun, one GPU each) the default mode cuts the one
+domain into N slabs along z, one per rank, that swap their three halo planes
+with their neighbours after every step over NCCL point to point (strong
+scaling: value = the domain's lattice updates per second); --mode replicas
+runs an independent copy per rank instead (weak scaling).  The populations
+(11.5 GB of reads and writes per step) are far larger than L2, so no flush is
+needed.
 """
 from __future__ import annotations
 
@@ -171,51 +176,95 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(budget_s: float = 15.0):
-    """The FP64 C oracle, single-threaded, on a bounded sample of the workload:
-    a 96 x 96 x 64 box of the same structure (walls, heated floor, liquid 16
-    deep, gravity), stepped until about `budget_s` seconds of CPU time."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_worker(args):
+    """One oracle process: a pool-boiling box of side (nx, ny, nz), `warmup`
+    untimed steps, then `steps` timed steps (or steps until `budget_s` when
+    steps is None).  Returns (nodes * steps, seconds, steps)."""
+    nx, ny, nz, depth, seed, warmup, steps, budget_s = args
     import oracle
     from paper_1705_10045_gb300 import workloads as W
-    nx, ny, nz = 96, 96, 64
-    f = W.pool_boiling_3d(nx=nx, ny=ny, nz=nz, T=0.8, depth=16, noise=1e-4, seed=3)
+    f = W.pool_boiling_3d(nx=nx, ny=ny, nz=nz, T=0.8, depth=depth, noise=1e-4, seed=seed)
     p = oracle.Params(Q=19, nx=nx, ny=ny, nz=nz, wall=True, T_fixed_lo=True, T_lo=0.95, g=(0.0, 0.0, -1e-5))
     s = oracle.State(p, f.rho, f.u, p.c_v * f.T)
+    if steps is None:
+        t0 = time.perf_counter()
+        s.step(1)
+        one = time.perf_counter() - t0
+        steps = max(1, int(budget_s / max(one, 1e-6)) - 1)
+    elif warmup:
+        s.step(warmup)
     t0 = time.perf_counter()
-    s.step(1)
-    one = time.perf_counter() - t0
-    n = max(1, int(budget_s / max(one, 1e-6)) - 1)
-    t0 = time.perf_counter()
-    s.step(n)
-    dt = time.perf_counter() - t0
-    return {"value": nx * ny * nz * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 C oracle, 1 thread, D3Q19 {nx}x{ny}x{nz} box of the same structure "
-                      f"(walls, heated floor, liquid 16 deep, gravity), {n} steps in {dt:.1f} s"}
+    s.step(steps)
+    return nx * ny * nz * steps, time.perf_counter() - t0, steps
+
+
+def oracle_on_cores(box, depth, processes, warmup=0, steps=None, budget_s=15.0):
+    """The FP64 C oracle, unchanged, as `processes` independent processes
+    (spawned, one box each, different noise seeds) on the host cores.
+    Returns (MLUPS over all processes, seconds of the slowest, steps each)."""
+    import multiprocessing as mp
+    jobs = [(*box, depth, 3 + i, warmup, steps, budget_s) for i in range(processes)]
+    if processes == 1:
+        res = [_oracle_worker(jobs[0])]
+    else:
+        with mp.get_context("spawn").Pool(processes) as pool:
+            res = pool.map(_oracle_worker, jobs)
+    wall = max(r[1] for r in res)
+    return sum(r[0] for r in res) / wall / 1e6, wall, res[0][2]
+
+
+def cpu_baseline(budget_s: float = 15.0):
+    """The FP64 C oracle on a bounded sample of the workload: a 96 x 96 x 64
+    box of the same structure (walls, heated floor, liquid 16 deep, gravity),
+    stepped for about `budget_s` seconds; once on one core, then as one
+    process per host core (the oracle is single-threaded; each process steps
+    its own box)."""
+    box = (96, 96, 64)
+    cores = os.cpu_count() or 1
+    one, wall1, n1 = oracle_on_cores(box, 16, 1, budget_s=budget_s)
+    many, wall_n, n_n = oracle_on_cores(box, 16, cores, steps=n1)
+    return {"value": many, "unit": "MLUPS", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"FP64 C oracle, {cores} processes (one per host core), each a D3Q19 96x96x64 box of the "
+                      f"same structure (walls, heated floor, liquid 16 deep, gravity), {n_n} steps in {wall_n:.1f} s",
+            "single_core": {"value": one, "unit": "MLUPS", "cores": 1,
+                            "sample": f"one process, {n1} steps in {wall1:.1f} s"}}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle on the host cores, each step one oracle
-    step of a 64 x 64 x 64 box of the workload's structure."""
+    """Reference arm: the FP64 oracle on the host cores, one process per core,
+    each stepping a 64 x 64 x 64 box of the workload's structure."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    import oracle
-    from paper_1705_10045_gb300 import workloads as W
     n = 64
-    f = W.pool_boiling_3d(nx=n, ny=n, nz=n, T=0.8, depth=16, noise=1e-4, seed=3)
-    p = oracle.Params(Q=19, nx=n, ny=n, nz=n, wall=True, T_fixed_lo=True, T_lo=0.95, g=(0.0, 0.0, -1e-5))
-    s = oracle.State(p, f.rho, f.u, p.c_v * f.T)
-    s.step(args.warmup)
-    t0 = time.perf_counter()
-    s.step(args.steps)
-    dt = time.perf_counter() - t0
-    v = n ** 3 * args.steps / dt / 1e6
+    cores = os.cpu_count() or 1
+    v, dt, _ = oracle_on_cores((n, n, n), 16, cores, warmup=args.warmup, steps=args.steps)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{n}^3 box of the same structure"},
-            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": f"FP64 C oracle, 1 thread, {n}^3 box, {args.steps} steps"},
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{cores} x {n}^3 boxes of the same structure"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                             "sample": f"FP64 C oracle, {cores} processes (one per host core), {n}^3 box each, "
+                                       f"{args.steps} steps"},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -435,6 +484,74 @@ def serving_bench(count: int = 24, storage: int = None, seed: int = 5, rate: flo
     }
 
 
+def slab_main(args, ws, rank, dist):
+    """One domain cut into `ws` z-slabs, slab r on rank r (slabs.SlabRank over
+    NCCL): every step launches the slab's fused step and swaps three halo
+    planes with each neighbour.  Timed like the undivided run; value is the
+    whole domain's MLUPS (strong scaling)."""
+    import torch
+    from paper_1705_10045_gb300 import lbm
+    from paper_1705_10045_gb300 import slabs as SL
+    stream = torch.cuda.current_stream()
+    dev = torch.cuda.current_device()
+    f = _fields()
+    nn = NX * NY * NZ
+    c_v = PARAMS["c_v"]
+    r = SL.SlabRank(dist, storage=lbm.LBM_STORE_FP32, device=dev, **PARAMS)
+    rho, u, eps = f.rho, np.ascontiguousarray(f.u), c_v * f.T
+    del f
+    r.init(rho, u, eps)
+    r.step(args.warmup)
+    prof = lbm.lbm_profile_step(r.h, max(3, min(20, args.steps // 10)))
+    own_nodes = NX * NY * r.slab.own
+    local_nodes = NX * NY * (r.slab.lo + r.slab.own + r.slab.hi)
+    halo_bytes = (r.slab.lo + r.slab.hi) * r.plane_bytes
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        e0.record(stream)
+        r.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    dist.barrier()
+    # end to end: host fields in, steps, owned planes' moments out
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    r.init(rho, u, eps)
+    r.step(args.steps)
+    out = r.moments()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    h2d = local_nodes * (2 + 3) * 8
+    d2h = sum(v.size for v in out.values()) * 8
+    r.close()
+    if rank == 0:
+        peak, peak_kind = _peak()
+        top = max(prof, key=prof.get)
+        achieved = 4 * 19 * 4 * local_nodes / (prof[top] * 1e-3) / 1e9
+        value = nn * args.steps / (ms * 1e-3) / 1e6
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": nn, "parallelism": f"z-slabs x{ws} (3 halo planes per cut)",
+                       "l2": "inputs larger than L2, no flush", "nodes_per_rank_owned": own_nodes,
+                       "nodes_per_rank_stepped": local_nodes},
+            "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "algorithmic_bytes_per_node": 4 * 19 * 4, "kernel_ms": prof},
+            "e2e": {"value": nn * args.steps / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps},
+            "halo_bytes_per_rank_per_step": halo_bytes * 2,
+            "gpu_launches": args.steps * (1 + 2 * ((r.slab.lo > 0) + (r.slab.hi > 0))),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -450,6 +567,8 @@ def main():
     ap.add_argument("--d2q9-size", default=None, help="NXxNY of a smaller D2Q9 domain (profiling)")
     ap.add_argument("--serve-jobs", type=int, default=24)
     ap.add_argument("--size", default=None, help="NXxNYxNZ of a smaller pool-boiling box (profiling)")
+    ap.add_argument("--mode", default="slabs", choices=["slabs", "replicas"],
+                    help="with several ranks: one domain in z-slabs (default) or a replica per rank")
     args = ap.parse_args()
     if args.size:
         _set_size(args.size)
@@ -466,6 +585,8 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if args.mode == "slabs":
+            return slab_main(args, ws, rank, dist)
     else:
         torch.cuda.set_device(local)
     from paper_1705_10045_gb300 import lbm
@@ -562,7 +683,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nodes": nn, "l2": f"inputs larger than L2 ({304 * nn / 1e9:.2f} GB of population "
-                       "traffic per step vs 129 MB L2), no flush", "parallelism": f"replicas x{ws}"},
+                       "traffic per step vs 129 MB L2), no flush",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "one GPU, undivided domain"},
             "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic_per_node * nn if traffic_per_node else None,

@@ -17,9 +17,13 @@
  *   5. BGK collision + EDM source for N (Eq. (lbe), Eq. (edm)) and, for the
  *      energy populations g (Eq. (gk)), BGK + g dE/E + the energy pseudoforce
  *      g^eq(E, u+du) - g^eq(E, u) (Sec. 4);
- *   6. streaming to x + c_k, periodic, or halfway bounce-back at walls on the
- *      last axis (y for D2Q9, z for D3Q19), optionally held at a fixed
- *      temperature through the conduction term.
+ *   6. streaming to x + c_k, periodic, or halfway bounce-back at walls
+ *      (per axis; each wall adiabatic or held at a fixed temperature through
+ *      the conduction term).  The paper's runs are periodic; a wall is the
+ *      halfway bounce-back of both population sets, and the stencils read
+ *      the mirror node beyond it (Phi and rho as they are, the velocity
+ *      component normal to the wall negated, T mirrored or reflected about
+ *      the wall temperature).
  *
  * Lattice units: h = dt = 1, theta = 1/3.  Velocity ordering: k = 0 rest,
  * then nearest neighbours, then next-nearest, each direction followed by its
@@ -55,14 +59,12 @@ extern "C" {
  * call is then not valid. */
 #define LBM_ERR_CUDA (-4)
 #define LBM_ERR_NONPHYSICAL (-5)
-/* A wait inside the fused step gave up: the producer and consumer warps of a
- * CTA hand planes over through shared-memory barriers whose waits are
- * bounded to about half a second, after which the CTA finishes without
- * waiting and counts the timeout.  Every synchronising call reports it until
- * lbm_init or lbm_set_state gives the handle a new state.  For tests, the
- * environment variable LBM_FAULT_DROP_HANDOFF=<plane>, read by lbm_create,
- * makes the first CTA of every fused step of that handle withhold the
- * hand-off of that plane, so that the wait runs out. */
+/* A wait inside the fused step gave up: the warps of a CTA hand planes over
+ * through shared-memory barriers whose waits are bounded to about half a
+ * second, after which the CTA finishes without waiting and counts the
+ * timeout.  Every synchronising call reports it until lbm_init or
+ * lbm_set_state gives the handle a new state.  lbm_test_drop_handoff makes
+ * such a wait run out on purpose (tests only). */
 #define LBM_ERR_TIMEOUT (-6)
 
 #define LBM_D2Q9 9
@@ -101,9 +103,14 @@ typedef struct lbm_params {
     int chi_mode;         /* 0: constant conductivity lambda; 1: lambda = rho c_v chi (Sec. 4) */
     double lambda, chi;
     double gravity[3];    /* body force per unit mass, added to F (Sec. 2: F is the total force) */
-    int wall;             /* last axis: 0 periodic, 1 bounce-back walls beyond both ends */
-    int T_fixed_lo, T_fixed_hi; /* per wall: 0 adiabatic, 1 held at T_lo / T_hi */
+    int wall;             /* last axis (y for D2Q9, z for D3Q19): 0 periodic, 1 bounce-back
+                             walls beyond both ends */
+    int T_fixed_lo, T_fixed_hi; /* per wall of the last axis: 0 adiabatic, 1 held at T_lo / T_hi */
     double T_lo, T_hi;
+    int wall_x;           /* x axis: 0 periodic, 1 bounce-back walls beyond both ends */
+    int wall_y;           /* y axis of D3Q19 (must be 0 for D2Q9, whose y is the last axis) */
+    int T_fixed_x[2], T_fixed_y[2]; /* per wall (low, high end): 0 adiabatic, 1 held at T_x[i] / T_y[i] */
+    double T_x[2], T_y[2];
     int pressure_work;    /* include -p div(u*) in dE (Sec. 4) */
     int conduction;       /* include div(lambda grad T) in dE (Sec. 4) */
     int pseudoforce;      /* include the energy pseudoforce (Sec. 4) */
@@ -166,8 +173,9 @@ int lbm_moments(lbm_handle* h, double* rho, double* u, double* T, double* P, int
  * step overwrites anyway.  Synchronising; errors as lbm_moments. */
 int lbm_moments_f(lbm_handle* h, float* rho, float* u, float* T, float* P, int mem);
 
-/* Global sums of the current state, reduced in FP64 with Kahan compensation in
- * a fixed order (bitwise reproducible): out[0] mass, out[1..3] momentum
+/* Global sums of the current state: each node's moments, formed in the
+ * arithmetic type, summed in FP64 with Kahan compensation in a fixed order
+ * (bitwise reproducible): out[0] mass, out[1..3] momentum
  * sum c_k N_k (x, y, z), out[4] internal energy, out[5] clamped nodes (U >= 0)
  * and out[6] non-finite or non-positive nodes since the last lbm_init,
  * out[7] steps taken since lbm_init.  Synchronising. */
@@ -204,15 +212,21 @@ void lbm_destroy(lbm_handle* h);
 
 /* ---------------------------------------------------------------------------
  * Batches: many independent domains (different sizes, same lattice and
- * storage) advanced together.  One kernel launch per step covers every
- * domain through a table of (domain, tile, chunk) work items; runs of 32
- * launches are captured in a CUDA graph and replayed.  Each domain keeps its
- * own state in its own device memory and has a step budget: lbm_batch_step(n)
- * advances every domain by min(n, its remaining budget) steps, so jobs with
- * different step counts share launches.  Results are bitwise identical to
- * running each domain alone with lbm_step (the per-node arithmetic is the
- * same kernel code).  The paper has no counterpart: this is the batched form
- * of its per-step update for many simulation jobs. */
+ * storage) advanced together.  lbm_batch_step(n) is one persistent kernel
+ * launch that covers every step of every domain through a table of
+ * (domain, tile, chunk) work items: CTAs take (step, item) work in order from
+ * a counter, and an item of step s of a domain starts once every item of that
+ * domain has finished step s - 1 (per-domain completion counters in device
+ * memory, waits bounded to about half a second, then LBM_ERR_TIMEOUT on that
+ * domain).  The request (clearing the counters, the launch, the descriptor
+ * bookkeeping) is captured in a CUDA graph and replayed.  Each domain keeps
+ * its own state in its own device memory and has a step budget:
+ * lbm_batch_step(n) advances every domain by min(n, its remaining budget)
+ * steps, so jobs with different step counts share the launch.  Results are
+ * bitwise identical to running each domain alone with lbm_step (the
+ * per-node arithmetic is the same kernel code).  The paper has no
+ * counterpart: this is the batched form of its per-step update for many
+ * simulation jobs. */
 typedef struct lbm_batch lbm_batch;
 
 /* Device memory in bytes a domain with parameters *p needs (admission control),
@@ -261,6 +275,15 @@ int lbm_batch_set_variant(lbm_batch* b, int v);
  * state and counters unchanged), keep the fastest, write its index to *best
  * and the mean ms per launch of shape v to ms[v] (ms may be NULL). */
 int lbm_batch_tune(lbm_batch* b, int reps, int* best, double* ms);
+
+/* Test hook, not for production runs: in the following lbm_batch_step
+ * requests, work item `item` of the table (0-based) does not report the end
+ * of its first step, so the next step's items of its domain wait until their
+ * bounded wait runs out and that domain reports LBM_ERR_TIMEOUT (a separately
+ * compiled instance of the batch kernel; the ordinary one has no trace of
+ * it).  item < 0 switches it off.  Errors: LBM_ERR_INVALID_ARG for a null
+ * batch. */
+int lbm_batch_test_drop_item(lbm_batch* b, int item);
 
 /* Wait for the batch's work; returns a latched device error of any domain. */
 int lbm_batch_sync(lbm_batch* b);
@@ -330,7 +353,7 @@ int lbm_slabs_step(lbm_slabs* s, int n);
 int lbm_slabs_moments(lbm_slabs* s, double* rho, double* u, double* T, double* P, int mem);
 
 /* As lbm_diagnostics for the whole domain: the sums over each slab's owned
- * planes (per-thread compensated, FP64 across threads and then across slabs
+ * planes (FP64 with Kahan compensation per thread, across threads and across slabs
  * in slab order); out[5], out[6] add up the slabs' counters, halo planes
  * included; out[7] the steps since lbm_slabs_init.  Synchronising. */
 int lbm_slabs_diagnostics(lbm_slabs* s, double out[8]);
@@ -373,12 +396,25 @@ int lbm_set_planes(lbm_handle* h, int first, int count, const void* buf, int mem
  * Scratch: a fixed 40,960-byte array in the library image, held by every
  * device that loads the library until exit.  The first call on a device
  * looks up that array's device address (with the device current) and should
- * come before any stream capture.  Calls share the array, so calls whose
- * kernels overlap on the GPU race; each call overwrites every partial it
- * reads.  Rejects null pointers, unknown lattice or storage, and sizes of
- * 2^31 nodes or more (LBM_ERR_INVALID_ARG); launch failures give LBM_ERR_CUDA. */
+ * come before any stream capture; the address is kept for the life of the
+ * process, so do not use the call on a device after cudaDeviceReset.  Calls
+ * share the array, so calls whose kernels overlap on the GPU race; calls
+ * ordered on one stream do not (each overwrites every partial it reads).
+ * Rejects null pointers, unknown lattice or storage, and sizes of 2^31 nodes
+ * or more, the largest domain lbm_create accepts (LBM_ERR_INVALID_ARG);
+ * launch failures give LBM_ERR_CUDA. */
 int lbm_conservation_sums_noalloc(int lattice, int storage, int nx, int ny, int nz, double rho_ref,
                                   double E_ref, const void* populations, double* sums, void* stream);
+
+/* Test hook, not for production runs.  From the next lbm_step on, the first
+ * CTA of every fused step of this handle withholds the hand-off of plane
+ * `plane` (index along the last lattice axis), so that its consumers' bounded
+ * wait runs out and the next synchronising call reports LBM_ERR_TIMEOUT;
+ * the steps run a separately compiled instance of the producer-load kernel
+ * that carries the hook (the kernels of ordinary steps have no trace of it).
+ * plane < 0 switches the hook off.  Errors: LBM_ERR_INVALID_ARG for a null
+ * handle. */
+int lbm_test_drop_handoff(lbm_handle* h, int plane);
 
 /* Message of the last error on this thread ("" if none). */
 const char* lbm_last_error(void);

@@ -24,6 +24,11 @@ template <typename R> KParams<R> make_kparams(const lbm_handle* h) {
     k.wall = q.wall != 0;
     k.T_fixed_lo = q.T_fixed_lo != 0; k.T_fixed_hi = q.T_fixed_hi != 0;
     k.T_lo = (R)q.T_lo; k.T_hi = (R)q.T_hi;
+    k.wall_x = q.wall_x != 0; k.wall_y = q.lattice == LBM_D3Q19 && q.wall_y != 0;
+    for (int e = 0; e < 2; ++e) {
+        k.T_fixed_x[e] = q.T_fixed_x[e] != 0; k.T_fixed_y[e] = q.T_fixed_y[e] != 0;
+        k.T_x[e] = (R)q.T_x[e]; k.T_y[e] = (R)q.T_y[e];
+    }
     k.pressure_work = q.pressure_work != 0; k.conduction = q.conduction != 0; k.pseudoforce = q.pseudoforce != 0;
     const bool shifted = q.storage == LBM_STORE_FP16;
     k.rho_ref = shifted ? (R)q.rho_ref : R(0);
@@ -48,17 +53,17 @@ template <> struct FusedTile<19, double> { static constexpr int TX = 32, TY = 8,
 
 // CTA shapes a batch may run with (TX x TY consumers + NP producers); the
 // autotuner times each on the batch and keeps the fastest.
+// MB: CTAs per SM the batch kernel is compiled for (its register cap).
 template <int Q, typename R, int V> struct BatchShape;
-template <typename R> struct BatchShape<9, R, 0> { static constexpr int TX = 128, TY = 1, NP = 160; };
-template <typename R> struct BatchShape<9, R, 1> { static constexpr int TX = 32, TY = 1, NP = 32; };
-template <typename R> struct BatchShape<9, R, 2> { static constexpr int TX = 64, TY = 1, NP = 64; };
-template <typename R> struct BatchShape<19, R, 0> { static constexpr int TX = 32, TY = 8, NP = 128; };
-template <typename R> struct BatchShape<19, R, 1> { static constexpr int TX = 32, TY = 8, NP = 160; };
-template <typename R> struct BatchShape<19, R, 2> { static constexpr int TX = 32, TY = 4, NP = 96; };
+template <typename R> struct BatchShape<9, R, 0> { static constexpr int TX = 128, TY = 1, NP = 160, MB = 3; };
+template <typename R> struct BatchShape<9, R, 1> { static constexpr int TX = 32, TY = 1, NP = 32, MB = 16; };
+template <typename R> struct BatchShape<9, R, 2> { static constexpr int TX = 64, TY = 1, NP = 64, MB = 8; };
+template <typename R> struct BatchShape<19, R, 0> { static constexpr int TX = 32, TY = 8, NP = 128, MB = 2; };
+template <typename R> struct BatchShape<19, R, 1> { static constexpr int TX = 32, TY = 8, NP = 160, MB = 2; };
+template <typename R> struct BatchShape<19, R, 2> { static constexpr int TX = 32, TY = 4, NP = 96, MB = 3; };
 
 template <int Q, typename S, typename R> struct Impl {
     static constexpr int TX = FusedTile<Q, R>::TX, TY = FusedTile<Q, R>::TY, NP = FusedTile<Q, R>::NP;
-
     static int launches(const lbm_handle* h) { return h->p.step_kernel == LBM_STEP_THREE_LAUNCH ? 3 : 1; }
 
     static MarchGeom geometry(const lbm_handle* h) {
@@ -78,13 +83,14 @@ template <int Q, typename S, typename R> struct Impl {
     static void launch_fused(lbm_handle* h, const KParams<R>& kp) {
         const MarchGeom G = geometry(h);
         const size_t smem = FusedShape<TX, TY>::template smem_bytes<R>();
-        auto kern = fused_step_kernel<Q, S, R, TX, TY, NP>;
+        const bool xw = h->p.wall_x || (Q == 19 && h->p.wall_y);
+        auto kern = xw ? fused_step_kernel<Q, S, R, TX, TY, NP, true> : fused_step_kernel<Q, S, R, TX, TY, NP, false>;
         if (!h->fused_ready) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             h->fused_ready = true;
         }
         const dim3 grid((G.na + TX - 1) / TX, (G.nb + TY - 1) / TY, (G.nm + G.chunk - 1) / G.chunk);
-        if (h->fault_drop > 0) {   // fault-injection test hook (LBM_FAULT_DROP_HANDOFF)
+        if (h->fault_drop > 0) {   // fault-injection test hook (lbm_test_drop_handoff)
             auto fk = fused_step_fault_kernel<Q, S, R, TX, TY, NP>;
             cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             fk<<<grid, TX * TY + NP, smem, h->stream>>>((const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], kp, G,
@@ -174,18 +180,24 @@ template <int Q, typename S, typename R> struct Impl {
     template <int V> struct Shape;
     static constexpr int kVariants = 3;
 
-    template <int BTX, int BTY, int BNP>
+    template <int BTX, int BTY, int BNP, int BMB>
     static MarchGeom batch_geometry(const lbm_handle* h) {
         MarchGeom G;
         G.na = h->p.nx;
         G.nb = Q == 9 ? 1 : h->p.ny;
         G.nm = Q == 9 ? h->p.ny : h->p.nz;
-        // chunks of 16 planes keep many CTAs per domain without much ring overlap
-        G.chunk = G.nm < 16 ? G.nm : 16;
+        // planes per work item: enough items for about four waves of two CTAs
+        // per SM when the domain runs alone (a step of a domain ends only when
+        // its last item does), between 8 and 64 planes (longer items cost
+        // less ring recompute)
+        const long long tiles = (long long)((G.na + BTX - 1) / BTX) * ((G.nb + BTY - 1) / BTY);
+        long long c = (G.nm * tiles + 4 * 304 - 1) / (4 * 304);
+        c = c < 8 ? 8 : (c > 64 ? 64 : c);
+        G.chunk = (int)(c > G.nm ? G.nm : c);
         return G;
     }
 
-    template <int BTX, int BTY, int BNP>
+    template <int BTX, int BTY, int BNP, int BMB>
     static int build_shape(lbm_batch* b) {
         std::vector<BatchItem> items;
         DomainDesc<R>* descs = (DomainDesc<R>*)b->h_descs;
@@ -194,7 +206,7 @@ template <int Q, typename S, typename R> struct Impl {
             DomainDesc<R> dd{};
             if (h) {
                 dd.kp = make_kparams<R>(h);
-                dd.G = batch_geometry<BTX, BTY, BNP>(h);
+                dd.G = batch_geometry<BTX, BTY, BNP, BMB>(h);
                 dd.pop[0] = h->pop[0];
                 dd.pop[1] = h->pop[1];
                 dd.cnt = (Counters*)h->cnt;
@@ -202,6 +214,7 @@ template <int Q, typename S, typename R> struct Impl {
                 dd.left = 0;
                 const int tx = (dd.G.na + BTX - 1) / BTX, ty = (dd.G.nb + BTY - 1) / BTY;
                 const int tz = (dd.G.nm + dd.G.chunk - 1) / dd.G.chunk;
+                dd.n_items = tx * ty * tz;
                 for (int z = 0; z < tz; ++z)
                     for (int y = 0; y < ty; ++y)
                         for (int x = 0; x < tx; ++x) items.push_back({(int)d, x * BTX, y * BTY, z * dd.G.chunk});
@@ -220,21 +233,51 @@ template <int Q, typename S, typename R> struct Impl {
             if (int rc = cuda_error(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(),
                                                     cudaMemcpyHostToDevice, b->stream), "batch table copy"))
                 return rc;
-        auto kern = fused_batch_kernel<Q, S, R, BTX, BTY, BNP>;
+        // one persistent CTA per resident slot: occupancy times the SM count
         const size_t smem = FusedShape<BTX, BTY>::template smem_bytes<R>();
-        return cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                          "batch kernel attribute");
+        b->xw = false;
+        for (auto* h : b->doms) b->xw = b->xw || (h && (h->p.wall_x || (Q == 19 && h->p.wall_y)));
+        const void* kerns[3] = {(const void*)fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, true, true>,
+                                (const void*)fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, true>,
+                                (const void*)fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, false>};
+        for (const void* kern : kerns)
+            if (int rc = cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                                    "batch kernel attribute"))
+                return rc;
+        int per_sm = 0, sms = 0;
+        if (int rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kerns[b->xw ? 1 : 2],
+                                                                              BTX * BTY + BNP, smem),
+                                "batch occupancy"))
+            return rc;
+        if (int rc = cuda_error(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->common.device),
+                                "SM count"))
+            return rc;
+        b->grid = std::max(1, per_sm) * std::max(1, sms);
+        return LBM_OK;
     }
 
-    template <int BTX, int BTY, int BNP>
-    static void launch_shape(lbm_batch* b, int s) {
+    // the persistent launch of a request (steps and scheduling state already in device memory)
+    template <int BTX, int BTY, int BNP, int BMB>
+    static void launch_shape(lbm_batch* b) {
         const size_t smem = FusedShape<BTX, BTY>::template smem_bytes<R>();
-        fused_batch_kernel<Q, S, R, BTX, BTY, BNP><<<b->n_items, BTX * BTY + BNP, smem, b->stream>>>(
-            (const BatchItem*)b->d_items, (const DomainDesc<R>*)b->d_descs, s);
+        const int n_doms = (int)b->doms.size();
+        const int grid = std::max(1, b->grid);   // CTAs beyond the work of a request leave at once
+        const auto* items = (const BatchItem*)b->d_items;
+        const auto* descs = (const DomainDesc<R>*)b->d_descs;
+        auto* sched = (BatchSched*)b->d_sched;
+        if (b->fault_item >= 0)
+            fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, true, true><<<grid, BTX * BTY + BNP, smem, b->stream>>>(
+                items, descs, b->n_items, sched, n_doms, b->fault_item);
+        else if (b->xw)
+            fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, true><<<grid, BTX * BTY + BNP, smem, b->stream>>>(
+                items, descs, b->n_items, sched, n_doms, -1);
+        else
+            fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, false><<<grid, BTX * BTY + BNP, smem, b->stream>>>(
+                items, descs, b->n_items, sched, n_doms, -1);
     }
 
     static int batch_build(lbm_batch* b);
-    static int batch_launch(lbm_batch* b, int s);
+    static int batch_launch(lbm_batch* b, int advance);
 
     static int reduce(lbm_handle* h, double* out_dev) {
         const KParams<R> kp = make_kparams<R>(h);
@@ -245,36 +288,31 @@ template <int Q, typename S, typename R> struct Impl {
     }
 };
 
-// descriptor bookkeeping after a replay of n launches: every domain took
-// min(n, left) steps
-template <typename R> __global__ void batch_advance_kernel(DomainDesc<R>* doms, int count, int n) {
-    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < count; d += gridDim.x * blockDim.x) {
-        const int taken = doms[d].left < n ? doms[d].left : n;
-        doms[d].cur ^= taken & 1;
-        doms[d].kp.step += (unsigned)taken;
-        doms[d].left -= taken;
-    }
-}
-
 template <int Q, typename S, typename R> int Impl<Q, S, R>::batch_build(lbm_batch* b) {
     switch (b->variant) {
-        case 0: return build_shape<BatchShape<Q, R, 0>::TX, BatchShape<Q, R, 0>::TY, BatchShape<Q, R, 0>::NP>(b);
-        case 1: return build_shape<BatchShape<Q, R, 1>::TX, BatchShape<Q, R, 1>::TY, BatchShape<Q, R, 1>::NP>(b);
-        default: return build_shape<BatchShape<Q, R, 2>::TX, BatchShape<Q, R, 2>::TY, BatchShape<Q, R, 2>::NP>(b);
+        case 0: return build_shape<BatchShape<Q, R, 0>::TX, BatchShape<Q, R, 0>::TY, BatchShape<Q, R, 0>::NP, BatchShape<Q, R, 0>::MB>(b);
+        case 1: return build_shape<BatchShape<Q, R, 1>::TX, BatchShape<Q, R, 1>::TY, BatchShape<Q, R, 1>::NP, BatchShape<Q, R, 1>::MB>(b);
+        default: return build_shape<BatchShape<Q, R, 2>::TX, BatchShape<Q, R, 2>::TY, BatchShape<Q, R, 2>::NP, BatchShape<Q, R, 2>::MB>(b);
     }
 }
 
-template <int Q, typename S, typename R> int Impl<Q, S, R>::batch_launch(lbm_batch* b, int s) {
-    if (s >= 0 && b->n_items > 0) {
+// One request: clear the scheduling state, the persistent launch, and (when
+// `advance`) the descriptor bookkeeping of the steps taken.
+template <int Q, typename S, typename R> int Impl<Q, S, R>::batch_launch(lbm_batch* b, int advance) {
+    if (b->n_items > 0) {
+        const size_t clear = sizeof(BatchSched) - sizeof(int) + 2 * sizeof(int) * b->doms.size();
+        if (int rc = cuda_error(cudaMemsetAsync((char*)b->d_sched + sizeof(int), 0, clear, b->stream), "batch clear"))
+            return rc;
         switch (b->variant) {
-            case 0: launch_shape<BatchShape<Q, R, 0>::TX, BatchShape<Q, R, 0>::TY, BatchShape<Q, R, 0>::NP>(b, s); break;
-            case 1: launch_shape<BatchShape<Q, R, 1>::TX, BatchShape<Q, R, 1>::TY, BatchShape<Q, R, 1>::NP>(b, s); break;
-            default: launch_shape<BatchShape<Q, R, 2>::TX, BatchShape<Q, R, 2>::TY, BatchShape<Q, R, 2>::NP>(b, s); break;
+            case 0: launch_shape<BatchShape<Q, R, 0>::TX, BatchShape<Q, R, 0>::TY, BatchShape<Q, R, 0>::NP, BatchShape<Q, R, 0>::MB>(b); break;
+            case 1: launch_shape<BatchShape<Q, R, 1>::TX, BatchShape<Q, R, 1>::TY, BatchShape<Q, R, 1>::NP, BatchShape<Q, R, 1>::MB>(b); break;
+            default: launch_shape<BatchShape<Q, R, 2>::TX, BatchShape<Q, R, 2>::TY, BatchShape<Q, R, 2>::NP, BatchShape<Q, R, 2>::MB>(b); break;
         }
     }
-    if (s < 0) {   // s < 0: descriptor advance after a replay of -s launches
+    if (advance && !b->doms.empty()) {
         const int count = (int)b->doms.size();
-        batch_advance_kernel<R><<<(count + 127) / 128, 128, 0, b->stream>>>((DomainDesc<R>*)b->d_descs, count, -s);
+        batch_advance_kernel<R><<<(count + 127) / 128, 128, 0, b->stream>>>((DomainDesc<R>*)b->d_descs, count,
+                                                                            (const BatchSched*)b->d_sched);
     }
     return cuda_error(cudaGetLastError(), "batch launch");
 }
@@ -321,7 +359,7 @@ template <int Q> const char* Backend<Q>::batch_variant_name(int v) {
     return Q == 9 ? n9[v] : n19[v];
 }
 template <int Q> int Backend<Q>::batch_build(lbm_batch* b) { LBM_BATCH_DISPATCH(b, batch_build(b)); }
-template <int Q> int Backend<Q>::batch_launch(lbm_batch* b, int s) { LBM_BATCH_DISPATCH(b, batch_launch(b, s)); }
+template <int Q> int Backend<Q>::batch_launch(lbm_batch* b, int advance) { LBM_BATCH_DISPATCH(b, batch_launch(b, advance)); }
 template <int Q> size_t Backend<Q>::desc_bytes(int storage) {
     return storage == LBM_STORE_FP64 ? sizeof(DomainDesc<double>) : sizeof(DomainDesc<float>);
 }

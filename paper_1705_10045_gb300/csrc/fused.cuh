@@ -118,7 +118,29 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 
 __device__ __forceinline__ int slotn(int m, int n) { return ((m % n) + n) % n; }
 
-template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
+// Coordinate of a ring row or column: wrapped on a periodic axis, the mirror
+// node across a wall (clamped into the axis for ring nodes of a ragged tile
+// that lie further out; their values are never used).
+__device__ __forceinline__ int ring_coord(int i, int n, int walled) {
+    if (!walled) return wrapi(i, n);
+    if (i < 0) i = -1 - i;
+    if (i >= n) i = 2 * n - 1 - i;
+    return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Walls beside tile-plane node (ga, gb): bit 0 / 1 the low / high wall of axis
+// a (x), bit 2 / 3 of axis b (y of D3Q19).
+template <typename R>
+__device__ __forceinline__ int wall_edges(const KParams<R>& p, int Q, int ga, int gb, int na, int nb) {
+    int e = 0;
+    if (p.wall_x) e |= (ga == 0 ? 1 : 0) | (ga == na - 1 ? 2 : 0);
+    if (Q == 19 && p.wall_y) e |= (gb == 0 ? 4 : 0) | (gb == nb - 1 ? 8 : 0);
+    return e;
+}
+
+// COH: read the populations through coherent loads (the persistent batch
+// kernel reads, in one launch, buffers that other CTAs wrote earlier in it).
+template <int Q, typename S, typename R, int TX, int TY, bool COH = false> struct FusedStages {
     using V = Vel<Q>;
     using M = MVel<Q>;
     using Sh = FusedShape<TX, TY>;
@@ -137,6 +159,12 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
     int plane_n;
     unsigned step;   // step counter of this launch (seeds FP16 stochastic rounding)
 
+    __device__ static R ld(const S* q, size_t i, R shift) {
+        return COH ? Store<S, R>::load_coh(q, i, shift) : Store<S, R>::load(q, i, shift);
+    }
+    __device__ static R ld_last(const S* q, size_t i, R shift) {
+        return COH ? Store<S, R>::load_last_coh(q, i, shift) : Store<S, R>::load_last(q, i, shift);
+    }
     __device__ R& phi(int slot, int r) const { return phis[slot * R_ + r]; }
     __device__ R& rut(int slot, int f, int r) const { return ruts[(slot * Sh::kRut + f) * F_ + r]; }
     __device__ R& du(int slot, int c, int r) const { return dus[(slot * 3 + c) * F_ + r]; }
@@ -159,8 +187,8 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
             R fN[Q], fG[Q];
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
-                fN[k] = Store<S, R>::load(src, (size_t)k * nn + n, R(V::w(k)) * p->rho_ref);
-                fG[k] = Store<S, R>::load(src, (size_t)(Q + k) * nn + n, R(V::w(k)) * p->E_ref);
+                fN[k] = ld(src, (size_t)k * nn + n, R(V::w(k)) * p->rho_ref);
+                fG[k] = ld(src, (size_t)(Q + k) * nn + n, R(V::w(k)) * p->E_ref);
             }
             R rho = 0, ja = 0, jb = 0, jm = 0, E = 0;
 #pragma unroll
@@ -227,9 +255,15 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         }
     }
 
-    // C: energy change, collision and push of the node (ta, tb) of plane c
-    __device__ void c_stage(int c, int ta, int tb, int n_ab, int dA_m, int dA_p, int dB_m, int dB_p,
+    // C: energy change, collision and push of the node (ta, tb) of plane c.
+    // edge: walls next to the node across the tile plane (bit 0 / 1: the low /
+    // high wall of axis a, bit 2 / 3: of axis b), from wall_edges().
+    // XW: the domain may have walls on the tile-plane axes (false: edge is 0
+    // and the wall handling across the tile compiles away).
+    template <bool XW>
+    __device__ void c_stage(int c, int ta, int tb, int n_ab, int dA_m, int dA_p, int dB_m, int dB_p, int edge_in,
                             Counters* cnt) const {
+        const int edge = XW ? edge_in : 0;
         const bool walls = p->wall;
         const int nm = G.nm;
         const R third = R(1.0 / 3.0);
@@ -242,7 +276,7 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
             const S* qg = src + n + (size_t)Q * nn;
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
-                hv[k] = Store<S, R>::load_last(qg, 0, R(V::w(k)) * p->E_ref);
+                hv[k] = ld_last(qg, 0, R(V::w(k)) * p->E_ref);
                 qg += nn;
             }
         }
@@ -255,17 +289,32 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         // finite-difference dE along a, b and the march axis (Sec. 4, Sec. 6.2)
         R div = 0, cond = 0;
         const R lc = conductivity(*p, rho);
-        auto axis = [&](R uu, R ud, R Tu, R Td, R ru, R rd) {
+        // one axis of the differences; g: bit 0 / 1 the low / high neighbour is
+        // the ghost beyond a wall, whose values are then own_u (normal
+        // velocity), T_lo / T_hi and the node's own density
+        auto axis = [&](R uu, R ud, R Tu, R Td, R ru, R rd, int g = 0, R own_u = R(0), R T_lo = R(0),
+                        R T_hi = R(0)) {
+            if (g) {
+                if (g & 2) { uu = own_u; Tu = T_hi; ru = rho; }
+                if (g & 1) { ud = own_u; Td = T_lo; rd = rho; }
+            }
             div += (uu - ud) / R(2);
             const R lu = (lc + conductivity(*p, ru)) / R(2);
             const R ld = (lc + conductivity(*p, rd)) / R(2);
             cond += lu * (Tu - T) - ld * (T - Td);
         };
+        // axes across the tile: neighbouring ring nodes, or (only for nodes
+        // beside a wall) the node itself mirrored across it: normal velocity
+        // negated, T mirrored or reflected about the wall temperature
         axis(rut(sr, 1, fc + 1) + du(sd, 0, fc + 1) / R(2), rut(sr, 1, fc - 1) + du(sd, 0, fc - 1) / R(2),
-             rut(sr, 4, fc + 1), rut(sr, 4, fc - 1), rut(sr, 0, fc + 1), rut(sr, 0, fc - 1));
+             rut(sr, 4, fc + 1), rut(sr, 4, fc - 1), rut(sr, 0, fc + 1), rut(sr, 0, fc - 1), edge & 3,
+             -(u[0] + dv[0] / R(2)), p->T_fixed_x[0] ? R(2) * p->T_x[0] - T : T,
+             p->T_fixed_x[1] ? R(2) * p->T_x[1] - T : T);
         if (Q == 19)
             axis(rut(sr, 2, fc + FW) + du(sd, 1, fc + FW) / R(2), rut(sr, 2, fc - FW) + du(sd, 1, fc - FW) / R(2),
-                 rut(sr, 4, fc + FW), rut(sr, 4, fc - FW), rut(sr, 0, fc + FW), rut(sr, 0, fc - FW));
+                 rut(sr, 4, fc + FW), rut(sr, 4, fc - FW), rut(sr, 0, fc + FW), rut(sr, 0, fc - FW), (edge >> 2) & 3,
+                 -(u[1] + dv[1] / R(2)), p->T_fixed_y[0] ? R(2) * p->T_y[0] - T : T,
+                 p->T_fixed_y[1] ? R(2) * p->T_y[1] - T : T);
         {   // march axis: neighbouring planes, or the node itself mirrored across a wall
             const bool gu = walls && c + 1 >= nm, gd = walls && c - 1 < 0;
             const int su = slotn(c + 1, Sh::kRutSlots), sdn = slotn(c - 1, Sh::kRutSlots);
@@ -298,6 +347,7 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
         // march axis periodic or bounced at a wall
         const int dM_m = (c == 0 ? nm - 1 : -1) * plane_n, dM_p = (c == nm - 1 ? 1 - nm : 1) * plane_n;
         const bool wall_lo = walls && c == 0, wall_hi = walls && c == nm - 1;
+        const bool edge_a_lo = edge & 1, edge_a_hi = edge & 2, edge_b_lo = edge & 4, edge_b_hi = edge & 8;
 
         // Collision, Eq. (lbe)/(edm)/(gk), written per node as
         //   N*_k = (1 - omega) N_k + rho (omega e0_k + de_k)
@@ -324,7 +374,9 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
                 const R fo = fma(fv, fN, fma(rho_om, e0, rho * de));
                 const R ho = fma(hvk, fG, fma(E_omE, e0, E_pf * de));
                 // push to x + c_k, or bounce back at a wall on the march axis
-                const bool bounce = WALL && ((M::m(k) == -1 && wall_lo) || (M::m(k) == 1 && wall_hi));
+                const bool bounce = WALL && ((M::m(k) == -1 && wall_lo) || (M::m(k) == 1 && wall_hi) ||
+                                             (M::a(k) == -1 && edge_a_lo) || (M::a(k) == 1 && edge_a_hi) ||
+                                             (M::b(k) == -1 && edge_b_lo) || (M::b(k) == 1 && edge_b_hi));
                 int to = 0;
                 if (M::a(k) == 1) to += dA_p; else if (M::a(k) == -1) to += dA_m;
                 if (M::b(k) == 1) to += dB_p; else if (M::b(k) == -1) to += dB_m;
@@ -345,7 +397,7 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
             };
             {
                 const R w0 = R(V::w(0));
-                emit(0, w0 * base0, w0 * dbase, Store<S, R>::load_last(qn, 0, w0 * p->rho_ref), hv[0]);
+                emit(0, w0 * base0, w0 * dbase, ld_last(qn, 0, w0 * p->rho_ref), hv[0]);
                 qn += nn;
             }
 #pragma unroll
@@ -357,14 +409,14 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
                 if (M::m(k) == 1) { cu += u[2]; cd += dv[2]; } else if (M::m(k) == -1) { cu -= u[2]; cd -= dv[2]; }
                 const R ev = wk * fma(R(4.5) * cu, cu, base0), od = (R(3) * wk) * cu;
                 const R dv_e = wk * fma(R(4.5) * cd, fma(R(2), cu, cd), dbase), dv_o = (R(3) * wk) * cd;
-                const R fa = Store<S, R>::load_last(qn, 0, wk * p->rho_ref);
-                const R fb = Store<S, R>::load_last(qn + nn, 0, wk * p->rho_ref);
+                const R fa = ld_last(qn, 0, wk * p->rho_ref);
+                const R fb = ld_last(qn + nn, 0, wk * p->rho_ref);
                 qn += 2 * nn;
                 emit(k, ev + od, dv_e + dv_o, fa, hv[k]);
                 emit(k + 1, ev - od, dv_e - dv_o, fb, hv[k + 1]);
             }
         };
-        if (wall_lo || wall_hi) collide(std::true_type{});
+        if (wall_lo || wall_hi || edge) collide(std::true_type{});
         else collide(std::false_type{});
     }
 };
@@ -374,11 +426,12 @@ template <int Q, typename S, typename R, int TX, int TY> struct FusedStages {
 // tile node), threads [TX*TY, TX*TY + NP) producers.
 // FAULT instantiates the fault-injection form: the first CTA withholds the
 // hand-off of plane fault_plane (tests of the bounded waits only).
-template <int Q, typename S, typename R, int TX, int TY, int NP, bool FAULT = false>
+template <int Q, typename S, typename R, int TX, int TY, int NP, bool FAULT = false, bool COH = false,
+          bool XW = true>
 __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restrict__ dst, const KParams<R>* p,
                                            const MarchGeom& G, unsigned step, int a0, int b0, int zb,
                                            Counters* cnt, unsigned char* smem_raw, int fault_plane = -1) {
-    using St = FusedStages<Q, S, R, TX, TY>;
+    using St = FusedStages<Q, S, R, TX, TY, COH>;
     using Sh = typename St::Sh;
     constexpr int NC = TX * TY, NT = NC + NP;
     St st;
@@ -398,8 +451,9 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restr
     const int tid = threadIdx.x;
     const int ze = min(zb + G.chunk, G.nm);
     const bool walls = p->wall;
-    for (int i = tid; i < Sh::RW; i += NT) st.ring_a[i] = wrapi(a0 + i - 2, G.na);
-    for (int i = tid; i < Sh::RH; i += NT) st.ring_b[i] = wrapi(b0 + i - Sh::RB, G.nb) * G.na;
+    const int wa = p->wall_x, wb = Q == 19 ? p->wall_y : 0;
+    for (int i = tid; i < Sh::RW; i += NT) st.ring_a[i] = ring_coord(a0 + i - 2, G.na, wa);
+    for (int i = tid; i < Sh::RH; i += NT) st.ring_b[i] = ring_coord(b0 + i - Sh::RB, G.nb, wb) * G.na;
 
     // hand-off ring: full[s] completes when the producers finish iteration u
     // (u = i - zb + 2, s = u mod D); empty[s] when every consumer has finished
@@ -454,28 +508,31 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restr
         const int n_ab = gb * G.na + ga;
         const int dA_m = ga == 0 ? G.na - 1 : -1, dA_p = ga == G.na - 1 ? 1 - G.na : 1;
         const int dB_m = (gb == 0 ? G.nb - 1 : -1) * G.na, dB_p = (gb == G.nb - 1 ? 1 - G.nb : 1) * G.na;
+        const int edge = XW ? wall_edges(*p, Q, ga, gb, G.na, G.nb) : 0;
         for (int c = zb; c < ze; ++c) {
             wait(full, c - zb + 4);
-            if (owns) st.c_stage(c, ta, tb, n_ab, dA_m, dA_p, dB_m, dB_p, cnt);
+            if (owns) st.template c_stage<XW>(c, ta, tb, n_ab, dA_m, dA_p, dB_m, dB_p, edge, cnt);
             mbar_arrive(empty + ((c - zb) % D));
         }
     }
 }
 
 // Single-domain fused step: CTA (x, y, z) takes tile (x TX, y TY) and the
-// z-th chunk of planes.
-template <int Q, typename S, typename R, int TX, int TY, int NP>
+// z-th chunk of planes.  XW: instance for domains with walls on the
+// tile-plane axes (the other instance carries no trace of them).
+template <int Q, typename S, typename R, int TX, int TY, int NP, bool XW>
 __global__ void __launch_bounds__(TX* TY + NP) fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst,
                                                                  KParams<R> p, MarchGeom G, Counters* cnt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_tile<Q, S, R, TX, TY, NP>(src, dst, &p, G, p.step, blockIdx.x * TX, blockIdx.y * TY,
-                                    blockIdx.z * G.chunk, cnt, smem_raw);
+    fused_tile<Q, S, R, TX, TY, NP, false, false, XW>(src, dst, &p, G, p.step, blockIdx.x * TX, blockIdx.y * TY,
+                                                      blockIdx.z * G.chunk, cnt, smem_raw);
 }
 
 // The same step with the fault-injection hook: the first CTA withholds the
 // hand-off of plane fault_plane, so that its consumers' bounded wait runs out
 // and the timeout is counted.  Launched only for handles created with
-// LBM_FAULT_DROP_HANDOFF set; the kernel above carries no trace of it.
+// the test hook lbm_test_drop_handoff set; the kernel above carries no trace
+// of it.
 template <int Q, typename S, typename R, int TX, int TY, int NP>
 __global__ void __launch_bounds__(TX* TY + NP) fused_step_fault_kernel(const S* __restrict__ src, S* __restrict__ dst,
                                                                        KParams<R> p, MarchGeom G, Counters* cnt,
@@ -486,10 +543,19 @@ __global__ void __launch_bounds__(TX* TY + NP) fused_step_fault_kernel(const S* 
 }
 
 // ---------------------------------------------------------------------------
-// Many domains in one launch.  Every CTA reads its work item (domain, tile,
-// chunk) from a table and the domain's descriptor; s is the step index within
-// a sequence of launches: a domain takes part while s < left and reads the
-// buffer (cur + s) mod 2.
+// Many domains, many steps, one persistent launch.  The work of a request is
+// n steps x the table of work items (domain, tile, chunk): work index
+// w = s * items + i is step s of item i.  CTAs take work indices in order from
+// a global counter.  An item of step s of domain d may start once every item
+// of d has finished step s - 1: its CTA waits (bounded) until the domain's
+// completion counter reaches s * items(d), reading it with acquire ordering;
+// a CTA that finishes an item adds 1 to the counter with release ordering.
+// Every item a CTA waits for has a smaller work index, so a CTA that is
+// running already holds it, and the waits always end: no deadlock, whatever
+// the number of CTAs that are resident.  A domain takes part while s < left
+// and reads buffer (cur + s) mod 2.  A wait that gives up counts a timeout
+// on the domain and marks it aborted, so that later items of that domain skip
+// their waits (and their results, which the latched LBM_ERR_TIMEOUT voids).
 
 struct BatchItem {
     int domain, a0, b0, zb;
@@ -502,22 +568,102 @@ template <typename R> struct DomainDesc {
     Counters* cnt;
     int cur;            // buffer holding the state at s = 0
     int left;           // steps the domain still takes, counted from s = 0
+    int n_items;        // work items of the domain in the table
 };
 
-template <int Q, typename S, typename R, int TX, int TY, int NP>
-__global__ void __launch_bounds__(TX* TY + NP) fused_batch_kernel(const BatchItem* __restrict__ items,
-                                                                  const DomainDesc<R>* __restrict__ doms, int s) {
+// Scheduling state of a request in device memory: steps, the next work
+// index, and per domain a completion counter and an abort flag.
+struct BatchSched {
+    int n_steps;
+    int next;
+    int pad[2];
+    // followed by unsigned done[domains], int aborted[domains]
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// FAULT: the item fault_item of step 0 does not report its completion
+// (tests of the bounded waits only).  XW: some domain has walls on the
+// tile-plane axes.
+template <int Q, typename S, typename R, int TX, int TY, int NP, int MB, bool FAULT, bool XW>
+__global__ void __launch_bounds__(TX* TY + NP, MB) fused_batch_kernel(const BatchItem* __restrict__ items,
+                                                                  const DomainDesc<R>* __restrict__ doms,
+                                                                  int n_items, BatchSched* sched, int n_doms,
+                                                                  int fault_item) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ KParams<R> kp;   // the domain's parameters, read once per CTA
-    const BatchItem it = items[blockIdx.x];
-    const DomainDesc<R>* d = doms + it.domain;
-    if (s >= d->left) return;   // the whole CTA leaves: its domain is done
-    if (threadIdx.x == 0) kp = d->kp;
-    const int in = (d->cur + s) & 1;
-    const MarchGeom G = d->G;
-    __syncthreads();
-    fused_tile<Q, S, R, TX, TY, NP>((const S*)d->pop[in], (S*)d->pop[in ^ 1], &kp, G, kp.step + (unsigned)s, it.a0,
-                                    it.b0, it.zb, d->cnt, smem_raw);
+    __shared__ KParams<R> kp;   // the current item's domain parameters
+    __shared__ int w_sh, go_sh;
+    int kp_domain = -1;         // domain whose parameters kp holds (thread 0)
+    unsigned* done = reinterpret_cast<unsigned*>(sched + 1);
+    int* aborted = reinterpret_cast<int*>(done + n_doms);
+    const long long total = (long long)sched->n_steps * n_items;
+    for (;;) {
+        if (threadIdx.x == 0) w_sh = atomicAdd(&sched->next, 1);
+        __syncthreads();
+        const long long w = w_sh;
+        if (w >= total || w < 0) break;
+        const int s = (int)(w / n_items), i = (int)(w % n_items);
+        const BatchItem it = items[i];
+        const DomainDesc<R>* d = doms + it.domain;
+        const bool active = s < d->left;
+        if (active && threadIdx.x == 0) {
+            if (kp_domain != it.domain) {   // consecutive items mostly share a domain
+                kp = d->kp;
+                kp_domain = it.domain;
+            }
+            int go = 1;
+            if (s > 0) {
+                const unsigned target = (unsigned)s * (unsigned)d->n_items;
+                const long long t0 = clock64();
+                while (ld_acquire_u32(done + it.domain) < target) {
+                    if (*(volatile int*)(aborted + it.domain)) {
+                        go = 0;
+                        break;
+                    }
+                    if (clock64() - t0 > 1000000000ll) {   // about half a second
+                        atomicExch(aborted + it.domain, 1);
+                        atomicAdd(&d->cnt->timeouts, 1ull);
+                        go = 0;
+                        break;
+                    }
+                }
+            }
+            go_sh = go;
+        }
+        __syncthreads();
+        if (active && go_sh) {
+            const int in = (d->cur + s) & 1;
+            const MarchGeom G = d->G;
+            fused_tile<Q, S, R, TX, TY, NP, false, true, XW>((const S*)d->pop[in], (S*)d->pop[in ^ 1], &kp, G,
+                                                         kp.step + (unsigned)s, it.a0, it.b0, it.zb, d->cnt,
+                                                         smem_raw);
+        }
+        __syncthreads();
+        if (active && threadIdx.x == 0) {
+            bool report = true;
+            if constexpr (FAULT) report = !(s == 0 && i == fault_item);
+            if (report) {
+                __threadfence();   // release: the item's stores before its completion
+                atomicAdd(done + it.domain, 1u);
+            }
+        }
+    }
+}
+
+// descriptor bookkeeping after a request of n steps: every domain took
+// min(n, left) steps
+template <typename R> __global__ void batch_advance_kernel(DomainDesc<R>* doms, int count, const BatchSched* sched) {
+    const int n = sched->n_steps;
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < count; d += gridDim.x * blockDim.x) {
+        const int taken = doms[d].left < n ? doms[d].left : n;
+        doms[d].cur ^= taken & 1;
+        doms[d].kp.step += (unsigned)taken;
+        doms[d].left -= taken;
+    }
 }
 
 }  // namespace lbm

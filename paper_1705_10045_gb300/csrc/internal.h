@@ -24,12 +24,13 @@ struct lbm_handle {
     long long steps = 0;
     bool initialised = false;
     bool fused_ready = false;   // shared-memory limit of the fused kernel raised
-    int fault_drop = 0;         // LBM_FAULT_DROP_HANDOFF test hook: 1 + plane, 0 = off
+    int fault_drop = 0;         // lbm_test_drop_handoff hook: 1 + plane, 0 = off
     cudaStream_t stream = nullptr;
 };
 
 // Many domains advanced together (lbm_batch_*): every domain is an
-// lbm_handle; one launch per step covers all of them through a work table.
+// lbm_handle; one persistent launch per request covers all of them and all
+// steps through a work table.
 struct lbm_batch {
     lbm_params common;
     int Q = 0;
@@ -45,13 +46,18 @@ struct lbm_batch {
     size_t descs_cap = 0;
     bool dirty = true;                  // work table out of date
     int variant = 0;                    // CTA shape (see lbm_batch_variants)
-    cudaGraphExec_t graph = nullptr;    // kGraphLaunches launches, s = 0..kGraphLaunches-1
-    int graph_items = -1, graph_variant = -1;
+    void* d_sched = nullptr;            // lbm::BatchSched + done[descs_cap] + aborted[descs_cap]
+    int* h_steps = nullptr;             // pinned staging of the request's step count
+    int sched_steps = 0;                // step count of the current request (host copy)
+    int grid = 0;                       // persistent CTAs of the current shape
+    bool xw = false;                    // some domain has walls on the tile-plane axes
+    int fault_item = -1;                // lbm_batch_test_drop_item hook: item of step 0, -1 = off
+    cudaGraphExec_t graph = nullptr;    // clear + persistent launch + descriptor advance
+    int graph_items = -1, graph_variant = -1, graph_doms = -1, graph_fault = -2;
 };
 
 namespace lbm {
 
-constexpr int kGraphLaunches = 32;
 
 // NVTX range around a library call: named spans on a profiler's timeline
 // (Nsight Systems), a cheap no-op when no tool is attached.
@@ -66,6 +72,7 @@ struct TraceRange {
 void set_error(const std::string& msg);
 int cuda_error(cudaError_t e, const char* where);
 
+
 // per-lattice entry points, dispatched on the storage format inside
 template <int Q> struct Backend {
     static int step(lbm_handle* h, int n);
@@ -76,11 +83,12 @@ template <int Q> struct Backend {
     static int moments(lbm_handle* h, double* rho, double* u, double* T, double* P);       // device pointers
     static int reduce(lbm_handle* h, double* out_dev);   // 5 sums into device memory
     static size_t field_bytes(int storage);
-    // batches: shapes, work table, descriptors and one launch of step s
+    // batches: shapes, work table, descriptors, and one request (clear, the
+    // persistent launch, and the descriptor advance when `advance`)
     static int batch_variants();
     static const char* batch_variant_name(int v);
     static int batch_build(lbm_batch* b);
-    static int batch_launch(lbm_batch* b, int s);
+    static int batch_launch(lbm_batch* b, int advance);
     static size_t desc_bytes(int storage);
 };
 

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) force_kernel(R* __restrict__ fld, KParams
     R s1x = 0, s1y = 0, s1z = 0, s2x = 0, s2y = 0, s2z = 0;
 #pragma unroll
     for (int k = 1; k < Q; ++k) {
-        Nb m = neighbour<V::D>(x, y, z, V::cx(k), V::cy(k), V::cz(k), p.nx, p.ny, p.nz, p.wall);
+        Nb m = neighbour<V::D>(x, y, z, V::cx(k), V::cy(k), V::cz(k), p);
         R ph = Phi[m.n];
         R t1 = R(V::G(k)) * ph * ph;
         R t2 = R(V::G(k)) * ph;
@@ -142,16 +142,16 @@ __global__ void __launch_bounds__(256) collide_kernel(const S* __restrict__ src,
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const int ex = a == 0, ey = a == 1, ez = a == 2;
-        Nb up = neighbour<D>(x, y, z, ex, ey, ez, p.nx, p.ny, p.nz, p.wall);
-        Nb dn = neighbour<D>(x, y, z, -ex, -ey, -ez, p.nx, p.ny, p.nz, p.wall);
+        Nb up = neighbour<D>(x, y, z, ex, ey, ez, p);
+        Nb dn = neighbour<D>(x, y, z, -ex, -ey, -ez, p);
         R uu = fld[(F_UX + a) * nn + up.n] + fld[(F_DUX + a) * nn + up.n] / R(2);
         R ud = fld[(F_UX + a) * nn + dn.n] + fld[(F_DUX + a) * nn + dn.n] / R(2);
-        if (up.ghost) uu = -uu;
-        if (dn.ghost) ud = -ud;
+        if (up.g[a]) uu = -uu;   // across a wall of axis a the normal velocity flips
+        if (dn.g[a]) ud = -ud;
         div += (uu - ud) / R(2);
-        R Tu = fld[F_T * nn + up.n], Td = fld[F_T * nn + dn.n];
-        if (up.ghost && p.T_fixed_hi) Tu = R(2) * p.T_hi - Tu;
-        if (dn.ghost && p.T_fixed_lo) Td = R(2) * p.T_lo - Td;
+        R Tu = fld[F_T * nn + up.n], Td = fld[F_T * nn + dn.n], Tw;
+        if (up.g[a] && wall_T<D>(p, a, 1, Tw)) Tu = R(2) * Tw - Tu;
+        if (dn.g[a] && wall_T<D>(p, a, 0, Tw)) Td = R(2) * Tw - Td;
         R lu = (lc + conductivity(p, fld[F_RHO * nn + up.n])) / R(2);
         R ld = (lc + conductivity(p, fld[F_RHO * nn + dn.n])) / R(2);
         cond += lu * (Tu - T) - ld * (T - Td);
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) collide_kernel(const S* __restrict__ src,
         const R fs = f + p.omega * (rho * e0 - f) + rho * de;
         R hs = h + p.omega_E * (E * e0 - h) + h * dEoverE;
         if (p.pseudoforce) hs += E * de;
-        Nb m = neighbour<D>(x, y, z, V::cx(k), V::cy(k), V::cz(k), p.nx, p.ny, p.nz, p.wall);
+        Nb m = neighbour<D>(x, y, z, V::cx(k), V::cy(k), V::cz(k), p);
         const int ko = m.ghost ? opposite(k) : k;
         const long long to = m.ghost ? i : m.n;
         Store<S, R>::store(dst, (size_t)ko * nn + to, fs, R(V::w(ko)) * p.rho_ref, slot_bits(nbits, k));
@@ -278,27 +278,26 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int Q, typename S, typename R>
 __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const S* __restrict__ pop, KParams<R> p,
                                                                 double* __restrict__ partials) {
-    // Each thread sums its nodes (about nn / 262144 of them) with compensation
-    // in the arithmetic type: the node moments are of that type already, and
-    // compensated FP32 keeps a partial to about one rounding of its value,
-    // while FP64 arithmetic runs at a small fraction of the FP32 rate on this
-    // GPU.  The partials are combined in FP64 from here on.
-    KahanT<R> acc[kSums];
+    // Each thread sums the moments of its nodes (about nn / 262144 of them,
+    // each formed in the arithmetic type as the step forms it) in FP64 with
+    // Kahan compensation; the partials are combined in FP64 from here on, in
+    // a fixed order, so the sums are FP64 and bitwise reproducible.
+    Kahan acc[kSums];
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.nn; i += stride) {
         R rho, jx, jy, jz, E;
         node_moments<Q, S, R>(pop, p.nn, i, p, rho, jx, jy, jz, E);
-        acc[0].add(rho);
-        acc[1].add(jx);
-        acc[2].add(jy);
-        acc[3].add(jz);
-        acc[4].add(E);
+        acc[0].add((double)rho);
+        acc[1].add((double)jx);
+        acc[2].add((double)jy);
+        acc[3].add((double)jz);
+        acc[4].add((double)E);
     }
     __shared__ double sh[kSums][kReduceThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < kSums; ++q) {
-        double v = warp_sum((double)acc[q].s - (double)acc[q].c);
+        double v = warp_sum(acc[q].s - acc[q].c);
         if (lane == 0) sh[q][warp] = v;
     }
     __syncthreads();

@@ -105,6 +105,18 @@ template <> struct Store<double, double> {
         return v;
     }
     __device__ static void store(double* p, size_t i, double v, double, unsigned = 0) { p[i] = v; }
+    // the same loads without the non-coherent path, for data other CTAs of
+    // the same launch wrote (read after an acquire of their release)
+    __device__ static double load_coh(const double* p, size_t i, double) {
+        double v;
+        asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p + i) : "memory");
+        return v;
+    }
+    __device__ static double load_last_coh(const double* p, size_t i, double) {
+        double v;
+        asm volatile("ld.global.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p + i) : "memory");
+        return v;
+    }
 };
 
 template <> struct Store<float, float> {
@@ -116,6 +128,16 @@ template <> struct Store<float, float> {
         return v;
     }
     __device__ static void store(float* p, size_t i, float v, float, unsigned = 0) { p[i] = v; }
+    __device__ static float load_coh(const float* p, size_t i, float) {
+        float v;
+        asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p + i) : "memory");
+        return v;
+    }
+    __device__ static float load_last_coh(const float* p, size_t i, float) {
+        float v;
+        asm volatile("ld.global.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p + i) : "memory");
+        return v;
+    }
 };
 
 template <> struct Store<__half, float> {
@@ -126,6 +148,16 @@ template <> struct Store<__half, float> {
     __device__ static float load_last(const __half* p, size_t i, float shift) {
         unsigned short b;
         asm("ld.global.nc.L1::no_allocate.b16 %0, [%1];" : "=h"(b) : "l"(p + i));
+        return __half2float(__ushort_as_half(b)) + shift;
+    }
+    __device__ static float load_coh(const __half* p, size_t i, float shift) {
+        unsigned short b;
+        asm volatile("ld.global.b16 %0, [%1];" : "=h"(b) : "l"(p + i) : "memory");
+        return __half2float(__ushort_as_half(b)) + shift;
+    }
+    __device__ static float load_last_coh(const __half* p, size_t i, float shift) {
+        unsigned short b;
+        asm volatile("ld.global.L1::no_allocate.b16 %0, [%1];" : "=h"(b) : "l"(p + i) : "memory");
         return __half2float(__ushort_as_half(b)) + shift;
     }
     // rnd13: 13 random bits; adding them below the 10 FP16 mantissa bits of
@@ -151,9 +183,12 @@ template <typename R> struct KParams {
     int chi_mode;
     R lambda, chi;
     R g[3];
-    int wall;
+    int wall;                       // walls of the last axis
     int T_fixed_lo, T_fixed_hi;
     R T_lo, T_hi;
+    int wall_x, wall_y;             // walls of x, and of y (D3Q19)
+    int T_fixed_x[2], T_fixed_y[2]; // per wall (low, high end)
+    R T_x[2], T_y[2];
     int pressure_work, conduction, pseudoforce;
     R rho_ref, E_ref;     // FP16 shifts
     unsigned step;        // step counter, seeds the FP16 stochastic rounding
@@ -196,45 +231,58 @@ __device__ __forceinline__ R latent_heat(const KParams<R>& p, R rho, R T, R div)
 }
 
 // ---------------------------------------------------------------------------
-// Neighbour index along the lattice with periodic x (and y for D3Q19) and a
-// periodic or walled last axis.  `ghost` is -1/+1 when the step crosses the
-// low/high wall; the index then points at the mirror node.
+// Neighbour index along the lattice.  Every axis is periodic or closed by
+// walls half a node beyond its ends (the last axis: `wall`; x: wall_x; y of
+// D3Q19: wall_y).  g[a] is -1/+1 when the step crosses the low/high wall of
+// lattice axis a and ghost is nonzero when it crosses any wall; the index
+// then points at the mirror node.
 
 struct Nb {
     long long n;
     int ghost;
+    int g[3];
 };
 
-template <int D>
-__device__ __forceinline__ Nb neighbour(int x, int y, int z, int dx, int dy, int dz, int nx, int ny,
-                                        int nz, int wall) {
+__device__ __forceinline__ int axis_step(int i, int n, int walled, int& g) {
+    g = 0;
+    if (!walled) return i < 0 ? i + n : (i >= n ? i - n : i);
+    if (i < 0) { g = -1; return -1 - i; }
+    if (i >= n) { g = 1; return 2 * n - 1 - i; }
+    return i;
+}
+
+template <int D, typename R>
+__device__ __forceinline__ Nb neighbour(int x, int y, int z, int dx, int dy, int dz, const KParams<R>& p) {
     Nb r;
-    r.ghost = 0;
-    int X = x + dx;
-    X = X < 0 ? X + nx : (X >= nx ? X - nx : X);
+    const int X = axis_step(x + dx, p.nx, p.wall_x, r.g[0]);
     int Y, Z;
     if (D == 2) {
+        Y = axis_step(y + dy, p.ny, p.wall, r.g[1]);
         Z = 0;
-        Y = y + dy;
-        if (wall) {
-            if (Y < 0) { Y = -1 - Y; r.ghost = -1; }
-            else if (Y >= ny) { Y = 2 * ny - 1 - Y; r.ghost = 1; }
-        } else {
-            Y = Y < 0 ? Y + ny : (Y >= ny ? Y - ny : Y);
-        }
+        r.g[2] = 0;
     } else {
-        Y = y + dy;
-        Y = Y < 0 ? Y + ny : (Y >= ny ? Y - ny : Y);
-        Z = z + dz;
-        if (wall) {
-            if (Z < 0) { Z = -1 - Z; r.ghost = -1; }
-            else if (Z >= nz) { Z = 2 * nz - 1 - Z; r.ghost = 1; }
-        } else {
-            Z = Z < 0 ? Z + nz : (Z >= nz ? Z - nz : Z);
-        }
+        Y = axis_step(y + dy, p.ny, p.wall_y, r.g[1]);
+        Z = axis_step(z + dz, p.nz, p.wall, r.g[2]);
     }
-    r.n = ((long long)Z * ny + Y) * nx + X;
+    r.ghost = r.g[0] | r.g[1] | r.g[2];
+    r.n = ((long long)Z * p.ny + Y) * p.nx + X;
     return r;
+}
+
+// Temperature mode of the wall at end `hi` (0 low, 1 high) of lattice axis a:
+// true and the wall temperature Tw when that wall is held at a fixed T.
+template <int D, typename R>
+__device__ __forceinline__ bool wall_T(const KParams<R>& p, int a, int hi, R& Tw) {
+    if (a == D - 1) {
+        Tw = hi ? p.T_hi : p.T_lo;
+        return hi ? p.T_fixed_hi : p.T_fixed_lo;
+    }
+    if (a == 0) {
+        Tw = p.T_x[hi];
+        return p.T_fixed_x[hi];
+    }
+    Tw = p.T_y[hi];
+    return p.T_fixed_y[hi];
 }
 
 // ---------------------------------------------------------------------------

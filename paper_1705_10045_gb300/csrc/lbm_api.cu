@@ -114,7 +114,8 @@ int sync_and_latch(lbm_handle* h) {
     rc = cuda_error(cudaStreamSynchronize(h->stream), "stream synchronize");
     if (rc) return rc;
     if (c.timeouts) {
-        set_error("fused step: a producer/consumer hand-off wait gave up (" + std::to_string(c.timeouts) +
+        set_error("fused step: a bounded wait gave up (a producer/consumer hand-off inside a CTA, or in a batch the "
+                  "wait for the domain's previous step; " + std::to_string(c.timeouts) +
                   " times); the state is not valid until lbm_init or lbm_set_state");
         return LBM_ERR_TIMEOUT;
     }
@@ -173,8 +174,12 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
         return LBM_ERR_INVALID_ARG;
     }
     const int last = p->lattice == LBM_D2Q9 ? p->ny : p->nz;
-    if (p->wall && last < 2) {
+    if ((p->wall && last < 2) || (p->wall_x && p->nx < 2) || (p->wall_y && p->ny < 2)) {
         set_error("a walled axis needs at least 2 nodes");
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (p->lattice == LBM_D2Q9 && p->wall_y) {
+        set_error("D2Q9: y is the last axis, its walls are `wall` (wall_y must be 0)");
         return LBM_ERR_INVALID_ARG;
     }
     if (!(p->tau > 0.5) || !(p->tau_E > 0.5) || !(p->c_v > 0.0) || !(p->kappa > 0.0)) {
@@ -214,13 +219,6 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
     h->nn = (long long)p->nx * p->ny * p->nz;
     h->elem = p->storage == LBM_STORE_FP64 ? 8 : (p->storage == LBM_STORE_FP32 ? 4 : 2);
     h->stream = (cudaStream_t)p->stream;
-    // fault injection for tests: the fused step's first CTA withholds the
-    // hand-off of this plane, so its consumers' bounded wait runs out
-    if (const char* f = std::getenv("LBM_FAULT_DROP_HANDOFF")) {
-        char* end = nullptr;
-        const long v = std::strtol(f, &end, 10);
-        if (end != f && v >= 0 && v < (1l << 30)) h->fault_drop = (int)v + 1;
-    }
     const size_t popb = (size_t)2 * h->Q * h->nn * h->elem;
     const size_t fldb = (h->Q == 9 ? lbm::Backend<9>::field_bytes(p->storage)
                                    : lbm::Backend<19>::field_bytes(p->storage)) * (size_t)h->nn;
@@ -525,6 +523,12 @@ void lbm_destroy(lbm_handle* h) {
     cudaFree(h->staging);
     cudaFree(h->coex);
     delete h;
+}
+
+int lbm_test_drop_handoff(lbm_handle* h, int plane) {
+    if (int rc = check_handle(h)) return rc;
+    h->fault_drop = plane < 0 ? 0 : plane + 1;
+    return LBM_OK;
 }
 
 const char* lbm_last_error(void) { return lbm::g_error.c_str(); }

@@ -1,13 +1,15 @@
 // Batches of domains advanced together (lbm_batch_* in include/lbm.h).
 //
 // Every domain is an ordinary lbm_handle (own population buffers, counters
-// and moments scratch), created on the batch's stream.  One launch per step
-// covers all domains through a table of work items (domain, tile, chunk);
-// each domain's descriptor in device memory holds its pointers, parameters,
-// the buffer holding its state and the steps it still takes in the current
-// request.  Runs of kGraphLaunches launches plus a descriptor-advance kernel
-// are captured once into a CUDA graph and replayed; there are no spin waits
-// between CTAs, the kernel boundaries order the steps.
+// and moments scratch), created on the batch's stream.  One persistent launch
+// per request covers every step of every domain through a table of work
+// items (domain, tile, chunk); each domain's descriptor in device memory
+// holds its pointers, parameters, the buffer holding its state and the steps
+// it still takes in the request.  Inside the launch, per-domain completion
+// counters order the steps (fused.cuh, fused_batch_kernel).  The request --
+// clearing the scheduling state, the launch and the descriptor advance -- is
+// captured once into a CUDA graph and replayed; the step count it reads is
+// uploaded with the descriptors.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -23,8 +25,8 @@ using lbm::set_error;
 namespace {
 
 int be_build(lbm_batch* b) { return b->Q == 9 ? lbm::Backend<9>::batch_build(b) : lbm::Backend<19>::batch_build(b); }
-int be_launch(lbm_batch* b, int s) {
-    return b->Q == 9 ? lbm::Backend<9>::batch_launch(b, s) : lbm::Backend<19>::batch_launch(b, s);
+int be_launch(lbm_batch* b, int advance) {
+    return b->Q == 9 ? lbm::Backend<9>::batch_launch(b, advance) : lbm::Backend<19>::batch_launch(b, advance);
 }
 size_t be_desc_bytes(const lbm_batch* b) {
     return b->Q == 9 ? lbm::Backend<9>::desc_bytes(b->common.storage) : lbm::Backend<19>::desc_bytes(b->common.storage);
@@ -49,7 +51,8 @@ int check_slot(const lbm_batch* b, int id) {
 void drop_graph(lbm_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
-    b->graph_items = b->graph_variant = -1;
+    b->graph_items = b->graph_variant = b->graph_doms = -1;
+    b->graph_fault = -2;
 }
 
 // Descriptor storage for every slot (device array + pinned staging).
@@ -58,19 +61,34 @@ int ensure_descs(lbm_batch* b) {
     if (need <= b->descs_cap) return LBM_OK;
     const size_t cap = std::max<size_t>(need, 2 * b->descs_cap);
     const size_t bytes = cap * be_desc_bytes(b);
-    void *d = nullptr, *h = nullptr;
+    const size_t sched = sizeof(lbm::BatchSched) + 2 * sizeof(int) * cap;
+    void *d = nullptr, *h = nullptr, *ds = nullptr;
     if (int rc = cuda_error(cudaMalloc(&d, bytes), "batch descriptors")) return rc;
-    if (int rc = cuda_error(cudaMallocHost(&h, bytes), "batch descriptor staging")) {
+    if (int rc = cuda_error(cudaMalloc(&ds, sched), "batch scheduling state")) {
         cudaFree(d);
         return rc;
     }
+    if (int rc = cuda_error(cudaMallocHost(&h, bytes), "batch descriptor staging")) {
+        cudaFree(d);
+        cudaFree(ds);
+        return rc;
+    }
     std::memset(h, 0, bytes);
+    if (!b->h_steps)
+        if (int rc = cuda_error(cudaMallocHost((void**)&b->h_steps, sizeof(int)), "batch step staging")) {
+            cudaFree(d);
+            cudaFree(ds);
+            cudaFreeHost(h);
+            return rc;
+        }
     if (b->d_descs) {
         cudaStreamSynchronize(b->stream);
         cudaFree(b->d_descs);
+        cudaFree(b->d_sched);
         cudaFreeHost(b->h_descs);
     }
     b->d_descs = d;
+    b->d_sched = ds;
     b->h_descs = h;
     b->descs_cap = cap;
     drop_graph(b);   // the graph baked the old descriptor address
@@ -102,9 +120,15 @@ template <typename R> void stage_descs(lbm_batch* b, long long n) {
     }
 }
 
+// descriptors and the request's step count (n <= 2^31 / items, see lbm_batch_step)
 int upload_descs(lbm_batch* b, long long n) {
     if (b->common.storage == LBM_STORE_FP64) stage_descs<double>(b, n);
     else stage_descs<float>(b, n);
+    *b->h_steps = (int)n;
+    b->sched_steps = (int)n;
+    if (int rc = cuda_error(cudaMemcpyAsync(b->d_sched, b->h_steps, sizeof(int), cudaMemcpyHostToDevice, b->stream),
+                            "batch step count copy"))
+        return rc;
     return cuda_error(cudaMemcpyAsync(b->d_descs, b->h_descs, b->doms.size() * be_desc_bytes(b), cudaMemcpyHostToDevice,
                                       b->stream),
                       "batch descriptor copy");
@@ -114,19 +138,19 @@ int capture_graph(lbm_batch* b) {
     cudaGraph_t g = nullptr;
     if (int rc = cuda_error(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture"))
         return rc;
-    int rc = LBM_OK;
-    for (int s = 0; s < lbm::kGraphLaunches && !rc; ++s) rc = be_launch(b, s);
-    if (!rc) rc = be_launch(b, -lbm::kGraphLaunches);
+    const int rc = be_launch(b, 1);
     const int rc_end = cuda_error(cudaStreamEndCapture(b->stream, &g), "graph capture end");
     if (rc || rc_end) {
         if (g) cudaGraphDestroy(g);
         return rc ? rc : rc_end;
     }
-    rc = cuda_error(cudaGraphInstantiate(&b->graph, g, 0), "graph instantiate");
+    const int rc_i = cuda_error(cudaGraphInstantiate(&b->graph, g, 0), "graph instantiate");
     cudaGraphDestroy(g);
-    if (rc) return rc;
+    if (rc_i) return rc_i;
     b->graph_items = b->n_items;
     b->graph_variant = b->variant;
+    b->graph_doms = (int)b->doms.size();
+    b->graph_fault = b->fault_item;
     return LBM_OK;
 }
 
@@ -246,18 +270,33 @@ int lbm_batch_step(lbm_batch* b, int n) {
         if (int rc = rebuild(b)) return rc;
     // the pinned staging may still feed the previous request's copy
     if (int rc = cuda_error(cudaStreamSynchronize(b->stream), "batch synchronize")) return rc;
-    if (int rc = upload_descs(b, n)) return rc;
-    const int full = n / lbm::kGraphLaunches, rem = n % lbm::kGraphLaunches;
-    if (full > 0 && (!b->graph || b->graph_items != b->n_items || b->graph_variant != b->variant)) {
-        drop_graph(b);
-        if (int rc = capture_graph(b)) return rc;
-    }
-    for (int r = 0; r < full; ++r)
+    // one request per chunk of steps small enough for 32-bit work indices
+    const long long per = std::max<long long>(1, (long long)(0x7FFFFFFF / std::max(1, b->n_items)) - 1);
+    for (long long done = 0; done < n;) {
+        const long long m = std::min<long long>(per, n - done);
+        if (int rc = upload_descs(b, m)) return rc;
+        if (!b->graph || b->graph_items != b->n_items || b->graph_variant != b->variant ||
+            b->graph_doms != (int)b->doms.size() || b->graph_fault != b->fault_item) {
+            drop_graph(b);
+            if (int rc = capture_graph(b)) return rc;
+        }
         if (int rc = cuda_error(cudaGraphLaunch(b->graph, b->stream), "graph launch")) return rc;
-    for (int s = 0; s < rem; ++s)
-        if (int rc = be_launch(b, s)) return rc;
-    if (rem > 0)
-        if (int rc = be_launch(b, -rem)) return rc;
+        done += m;
+        if (done < n)   // the staging feeds the next chunk's copies
+            if (int rc = cuda_error(cudaStreamSynchronize(b->stream), "batch synchronize")) return rc;
+        for (size_t d = 0; d < b->doms.size() && done < n; ++d) {
+            lbm_handle* h = b->doms[d];
+            if (!h) continue;
+            const long long taken = std::min<long long>(b->budget[d], m);
+            h->cur ^= (int)(taken & 1);
+            h->steps += taken;
+            b->budget[d] -= taken;
+        }
+        if (done >= n) {
+            n = m;   // the mirrors below account for the last chunk
+            break;
+        }
+    }
     // host mirrors follow the same arithmetic as the device descriptors
     for (size_t d = 0; d < b->doms.size(); ++d) {
         lbm_handle* h = b->doms[d];
@@ -350,7 +389,7 @@ int lbm_batch_tune(lbm_batch* b, int reps, int* best, double* ms) {
         for (auto& x : b->budget) x = 1;
         if ((rc = upload_descs(b, 1))) break;
         b->budget = keep;
-        rc = be_launch(b, 0);   // warm-up
+        rc = be_launch(b, 0);   // warm-up: one step into the spare buffers, no descriptor advance
         cudaEventRecord(e0, b->stream);
         for (int r = 0; r < reps && !rc; ++r) rc = be_launch(b, 0);
         cudaEventRecord(e1, b->stream);
@@ -375,6 +414,12 @@ int lbm_batch_tune(lbm_batch* b, int reps, int* best, double* ms) {
     return rc;
 }
 
+int lbm_batch_test_drop_item(lbm_batch* b, int item) {
+    if (int rc = check_batch(b)) return rc;
+    b->fault_item = item < 0 ? -1 : item;
+    return LBM_OK;
+}
+
 int lbm_batch_sync(lbm_batch* b) {
     lbm::TraceRange trace_("lbm_batch_sync");
     if (int rc = check_batch(b)) return rc;
@@ -393,7 +438,9 @@ void lbm_batch_destroy(lbm_batch* b) {
     for (auto* h : b->doms) lbm_destroy(h);
     cudaFree(b->d_items);
     cudaFree(b->d_descs);
+    cudaFree(b->d_sched);
     cudaFreeHost(b->h_descs);
+    cudaFreeHost(b->h_steps);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }

@@ -13,9 +13,12 @@
 // code is only a host-side stand-in, so the device address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, by the
 // first call made on it; that first call should come before any stream
-// capture.  All calls share the array: the reduction overwrites every block
-// partial it reads, so nothing has to start at zero, but two calls whose
-// kernels overlap on the GPU (different streams without ordering) race on it.
+// capture.  The address is kept for the life of the process, so the call must
+// not be used on a device after cudaDeviceReset (which unloads the library's
+// device image).  All calls share the array: the reduction overwrites every
+// block partial it reads, so nothing has to start at zero, but two calls
+// whose kernels overlap on the GPU (different streams without ordering) race
+// on it.
 #include <mutex>
 #include <string>
 
@@ -83,8 +86,8 @@ extern "C" int lbm_conservation_sums_noalloc(int lattice, int storage, int nx, i
         return LBM_ERR_INVALID_ARG;
     }
     if ((long long)nx * ny * nz >= (1ll << 31)) {
-        lbm::set_error("lbm_conservation_sums_noalloc: at most 2^31 - 1 nodes (the static scratch is sized "
-                       "for 1024 blocks of a grid-stride reduction over 32-bit node indices)");
+        lbm::set_error("lbm_conservation_sums_noalloc: at most 2^31 - 1 nodes, the largest domain lbm_create "
+                       "accepts");
         return LBM_ERR_INVALID_ARG;
     }
     if (storage < LBM_STORE_FP64 || storage > LBM_STORE_FP16) {

@@ -115,22 +115,22 @@ __global__ void __launch_bounds__(lbm::kReduceThreads) range_reduce_kernel(const
                                                                           long long i0, long long n,
                                                                           lbm::KParams<R> p,
                                                                           double* __restrict__ partials) {
-    lbm::KahanT<R> acc[lbm::kSums];
+    lbm::Kahan acc[lbm::kSums];   // FP64, compensated, as the whole-domain sums
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
         R rho, jx, jy, jz, E;
         lbm::node_moments<Q, S, R>(pop, nn, i0 + t, p, rho, jx, jy, jz, E);
-        acc[0].add(rho);
-        acc[1].add(jx);
-        acc[2].add(jy);
-        acc[3].add(jz);
-        acc[4].add(E);
+        acc[0].add((double)rho);
+        acc[1].add((double)jx);
+        acc[2].add((double)jy);
+        acc[3].add((double)jz);
+        acc[4].add((double)E);
     }
     __shared__ double sh[lbm::kSums][lbm::kReduceThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < lbm::kSums; ++q) {
-        double v = lbm::warp_sum((double)acc[q].s - (double)acc[q].c);
+        double v = lbm::warp_sum(acc[q].s - acc[q].c);
         if (lane == 0) sh[q][warp] = v;
     }
     __syncthreads();

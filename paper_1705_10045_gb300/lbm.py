@@ -65,6 +65,9 @@ class lbm_params(ctypes.Structure):
         ("gravity", ctypes.c_double * 3),
         ("wall", ctypes.c_int), ("T_fixed_lo", ctypes.c_int), ("T_fixed_hi", ctypes.c_int),
         ("T_lo", ctypes.c_double), ("T_hi", ctypes.c_double),
+        ("wall_x", ctypes.c_int), ("wall_y", ctypes.c_int),
+        ("T_fixed_x", ctypes.c_int * 2), ("T_fixed_y", ctypes.c_int * 2),
+        ("T_x", ctypes.c_double * 2), ("T_y", ctypes.c_double * 2),
         ("pressure_work", ctypes.c_int), ("conduction", ctypes.c_int), ("pseudoforce", ctypes.c_int),
         ("latent", ctypes.c_double),
         ("storage", ctypes.c_int), ("rho_ref", ctypes.c_double), ("E_ref", ctypes.c_double),
@@ -120,6 +123,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_coexistence.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)]
     lib.lbm_coexistence.restype = ctypes.c_int
+    lib.lbm_test_drop_handoff.argtypes = [H, ctypes.c_int]
+    lib.lbm_test_drop_handoff.restype = ctypes.c_int
     lib.lbm_last_error.argtypes = []
     lib.lbm_last_error.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_init", "lbm_step", "lbm_moments", "lbm_diagnostics", "lbm_get_state",
@@ -144,6 +149,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_batch_set_variant.argtypes = [B, ctypes.c_int]
     lib.lbm_batch_tune.argtypes = [B, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     lib.lbm_batch_sync.argtypes = [B]
+    lib.lbm_batch_test_drop_item.argtypes = [B, ctypes.c_int]
+    lib.lbm_batch_test_drop_item.restype = ctypes.c_int
     lib.lbm_batch_destroy.argtypes = [B]
     lib.lbm_batch_destroy.restype = None
     S = ctypes.c_void_p
@@ -225,6 +232,10 @@ def make_params(**kw) -> lbm_params:
             k = "lambda_"
         if k == "gravity":
             p.gravity = (ctypes.c_double * 3)(*[float(x) for x in v])
+        elif k in ("T_fixed_x", "T_fixed_y"):
+            setattr(p, k, (ctypes.c_int * 2)(*[int(x) for x in v]))
+        elif k in ("T_x", "T_y"):
+            setattr(p, k, (ctypes.c_double * 2)(*[float(x) for x in v]))
         elif k == "stream":
             p.stream = ctypes.c_void_p(int(v) if v is not None else 0)
         else:
@@ -335,6 +346,12 @@ def lbm_profile_step(h, n: int) -> dict:
 
 def lbm_launch_name(h, j: int) -> str:
     return load().lbm_launch_name(h, int(j)).decode()
+
+
+def lbm_test_drop_handoff(h, plane: int):
+    """Test hook: the first CTA of every fused step withholds the hand-off of
+    `plane` (plane < 0: off), so that a bounded wait runs out."""
+    _check(load().lbm_test_drop_handoff(h, int(plane)))
 
 
 def lbm_destroy(h):

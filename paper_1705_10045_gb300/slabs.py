@@ -69,7 +69,13 @@ class SlabRank:
         import torch
         self.dist, self.group = dist, group
         self.rank, self.world = dist.get_rank(group), dist.get_world_size(group)
-        kw.setdefault("stream", torch.cuda.current_stream().cuda_stream)
+        # the plane copies are enqueued on the handle's stream and the sends,
+        # receives and buffer lifetimes are ordered on torch's current stream:
+        # the two must be the same stream
+        current = torch.cuda.current_stream().cuda_stream
+        if kw.get("stream") not in (None, current):
+            raise ValueError("SlabRank runs on torch's current stream; make the intended stream current instead")
+        kw["stream"] = current
         self.params = lbm.make_params(**kw)
         self.slab = lbm.lbm_slab_plan(self.params, self.world, self.rank)
         self.h = lbm.lbm_create(self.slab.p)

@@ -59,6 +59,37 @@ def test_noalloc_sums_match_diagnostics_on_two_calls(lattice, storage):
         sim.close()
 
 
+def test_noalloc_two_ordered_calls_on_one_stream():
+    """Two states summed by two calls queued back to back on one non-default
+    stream, with a single synchronisation at the end: the calls share the
+    scratch array, and stream order alone keeps them apart."""
+    import torch
+    sims, states = [], []
+    try:
+        for seed, steps in ((3, 5), (4, 11)):
+            f = W.pool_boiling_3d(nx=64, ny=40, nz=24, T=0.8, depth=8, noise=1e-3, seed=seed)
+            sim = lbm.Lbm(lattice=19, nx=64, ny=40, nz=24, wall=1, T_fixed_lo=1, T_lo=0.95,
+                          storage=lbm.LBM_STORE_FP32)
+            sim.init(f.rho, f.u, 1.5 * f.T)
+            sim.step(steps)
+            sims.append(sim)
+            states.append(_device_state(sim))
+        torch.cuda.synchronize()
+        stream = torch.cuda.Stream()
+        outs = [torch.full((5,), float("nan"), dtype=torch.float64, device="cuda") for _ in sims]
+        for sim, st, out in zip(sims, states, outs):
+            p = sim.params
+            lbm.lbm_conservation_sums_noalloc(p.lattice, p.storage, p.nx, p.ny, p.nz, p.rho_ref, p.E_ref,
+                                              st.data_ptr() + HEADER, out.data_ptr(), stream.cuda_stream)
+        stream.synchronize()
+        for sim, out in zip(sims, outs):
+            want = lbm.lbm_diagnostics(sim.h)[:5]
+            np.testing.assert_allclose(out.cpu().numpy(), want, rtol=0, atol=1e-12 * abs(want[0]))
+    finally:
+        for sim in sims:
+            sim.close()
+
+
 def test_noalloc_rejects_bad_sizes_and_pointers():
     import torch
     L = lbm.load()

@@ -50,18 +50,39 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
 }
 // Wait until the phase of parity `parity` of *b has completed, for at most
-// about half a second (1e9 clock cycles); false when the wait gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
-    const long long t0 = clock64();
-    while (clock64() - t0 < 1000000000ll) {
-        unsigned done;
+// about half a second (1e9 clock cycles); false when the wait gave up.  Each
+// try_wait may suspend the warp for up to kWaitHintNs nanoseconds; it resumes
+// as soon as the phase completes, so the hint bounds how often a waiting warp
+// polls (and takes issue slots from the working warps), not its latency.
+#ifndef LBM_WAIT_HINT_NS
+#define LBM_WAIT_HINT_NS 20000
+#endif
+constexpr unsigned kWaitHintNs = LBM_WAIT_HINT_NS;
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
+    unsigned done;
+    if (kWaitHintNs > 0) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(b)), "r"(parity), "n"(kWaitHintNs)
+            : "memory");
+    } else {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
             : "r"(smem_addr(b)), "r"(parity)
             : "memory");
-        if (done) return true;
     }
+    return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+    if (mbar_try_wait(b, parity)) return true;
+    const long long t0 = clock64();
+    do {
+        if (mbar_try_wait(b, parity)) return true;
+    } while (clock64() - t0 < 1000000000ll);
     return false;
 }
 

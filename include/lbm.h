@@ -183,7 +183,10 @@ int lbm_diagnostics(lbm_handle* h, double out[8]);
 
 /* Size in bytes of the raw state for lbm_get_state / lbm_set_state: a
  * 16-byte header (magic "LBM1", lattice, storage, step count) followed by the
- * 2Q population planes (N then g) in the storage format. */
+ * 2Q population planes N_0..N_{Q-1}, g_0..g_{Q-1} (each nx*ny*nz values, x
+ * fastest) in the storage format.  On the device the library keeps the two
+ * sets interleaved (for each k the node pairs (N_k, g_k)); lbm_get_state and
+ * lbm_set_state convert, using the handle's idle population buffer. */
 size_t lbm_state_bytes(const lbm_handle* h);
 
 /* Copy the raw state out or in (checkpoint / resume; resuming is bitwise
@@ -365,13 +368,13 @@ int lbm_slabs_sync(lbm_slabs* s);
 void lbm_slabs_destroy(lbm_slabs* s);
 
 /* Halo exchange between processes (one slab handle per process): bytes of one
- * plane of the last axis over all 2Q population arrays in the handle's
- * storage format. */
+ * plane of the last axis over all 2Q populations in the handle's storage
+ * format. */
 size_t lbm_plane_bytes(const lbm_handle* h);
 
 /* Copy planes [first, first + count) of the current populations out of / into
- * buf, laid out as 2Q rows (N_0..N_{Q-1}, g_0..g_{Q-1}) of count planes each,
- * storage format.  mem = LBM_MEM_DEVICE: one kernel on the handle's stream,
+ * buf in the device layout: Q rows (k = 0..Q-1) of count planes each, every
+ * node a pair (N_k, g_k), storage format.  mem = LBM_MEM_DEVICE: one kernel on the handle's stream,
  * asynchronous (the caller orders its own use of buf on that stream or
  * synchronises); LBM_MEM_HOST: synchronising.  Errors (LBM_ERR_INVALID_ARG):
  * null pointers, bad mem flag, no state yet, planes outside the handle's

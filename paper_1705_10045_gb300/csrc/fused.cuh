@@ -180,11 +180,14 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false> struc
     int plane_n;
     unsigned step;   // step counter of this launch (seeds FP16 stochastic rounding)
 
-    __device__ static R ld(const S* q, size_t i, R shift) {
-        return COH ? Store<S, R>::load_coh(q, i, shift) : Store<S, R>::load(q, i, shift);
+    // the pair (N_k, g_k) at pair index i of q
+    __device__ static void ld2(const S* q, size_t i, R sN, R sG, R& a, R& b) {
+        if (COH) Store<S, R>::load2_coh(q, i, sN, sG, a, b);
+        else Store<S, R>::load2(q, i, sN, sG, a, b);
     }
-    __device__ static R ld_last(const S* q, size_t i, R shift) {
-        return COH ? Store<S, R>::load_last_coh(q, i, shift) : Store<S, R>::load_last(q, i, shift);
+    __device__ static void ld2_last(const S* q, size_t i, R sN, R sG, R& a, R& b) {
+        if (COH) Store<S, R>::load2_last_coh(q, i, sN, sG, a, b);
+        else Store<S, R>::load2_last(q, i, sN, sG, a, b);
     }
     __device__ R& phi(int slot, int r) const { return phis[slot * R_ + r]; }
     __device__ R& rut(int slot, int f, int r) const { return ruts[(slot * Sh::kRut + f) * F_ + r]; }
@@ -207,10 +210,8 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false> struc
             const size_t n = (size_t)(plane_off + ring_b[rb] + ring_a[ra]);
             R fN[Q], fG[Q];
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                fN[k] = ld(src, (size_t)k * nn + n, R(V::w(k)) * p->rho_ref);
-                fG[k] = ld(src, (size_t)(Q + k) * nn + n, R(V::w(k)) * p->E_ref);
-            }
+            for (int k = 0; k < Q; ++k)
+                ld2(src, pair_index(k, nn, n), R(V::w(k)) * p->rho_ref, R(V::w(k)) * p->E_ref, fN[k], fG[k]);
             R rho = 0, ja = 0, jb = 0, jm = 0, E = 0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
@@ -288,17 +289,18 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false> struc
         const bool walls = p->wall;
         const int nm = G.nm;
         const R third = R(1.0 / 3.0);
-        // the node's g populations first: their loads are in flight while the
+        // the node's populations first: their loads are in flight while the
         // finite differences below read shared memory.  The reload is the last
         // use of these lines on this SM, so it does not allocate them in L1.
+        // The pointer walks from one direction's pair array to the next.
         const int n = c * plane_n + n_ab;
-        R hv[Q];
+        R fv[Q], hv[Q];
         {
-            const S* qg = src + n + (size_t)Q * nn;
+            const S* q = src + 2 * (size_t)n;
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
-                hv[k] = ld_last(qg, 0, R(V::w(k)) * p->E_ref);
-                qg += nn;
+                ld2_last(q, 0, R(V::w(k)) * p->rho_ref, R(V::w(k)) * p->E_ref, fv[k], hv[k]);
+                q += 2 * nn;
             }
         }
         const int sr = slotn(c, Sh::kRutSlots), sd = slotn(c, Sh::kDuSlots);
@@ -356,9 +358,6 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false> struc
         if (p->latent != R(0)) dE += latent_heat(*p, rho, T, div);
         if (P - rho * third >= R(0)) atomicAdd(&cnt->clamps, 1ull);
 
-        // the node's N population k sits at qn + k nn; the pointer walks from
-        // one population to the next
-        const S* qn = src + n;
         R E = 0;
 #pragma unroll
         for (int k = 0; k < Q; ++k) E += hv[k];
@@ -385,8 +384,7 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false> struc
         const R fN = R(1) - om, fG = R(1) - omE + dEoverE;
         const R rho_om = rho * om, E_omE = E * omE, E_pf = p->pseudoforce ? E : R(0);
         const unsigned nbits = Store<S, R>::kStochastic ? node_bits(step, (unsigned)n) : 0u;
-        S* dn = dst + n;                    // population k of the node's slot, N set
-        S* dg = dn + (size_t)Q * nn;        // and g set
+        S* dk = dst + 2 * (size_t)n;        // pair k of the node's slot (walks over k)
         // the collision and push, instantiated once for planes next to a wall
         // (WALL: some directions bounce back) and once for all other planes
         auto collide = [&](auto wall_tag) {
@@ -405,21 +403,13 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false> struc
                 // opposite directions share a weight, so the FP16 shift of slot ko is w_k ref
                 const R wk = R(V::w(k));
                 const unsigned rN = slot_bits(nbits, k), rG = slot_bits(nbits, Q + k);
-                if (bounce) {
-                    const long long back = (long long)(opposite(k) - k) * (long long)nn;
-                    Store<S, R>::store(dn + back, 0, fo, wk * p->rho_ref, rN);
-                    Store<S, R>::store(dg + back, 0, ho, wk * p->E_ref, rG);
-                } else {
-                    Store<S, R>::store(dn + to, 0, fo, wk * p->rho_ref, rN);
-                    Store<S, R>::store(dg + to, 0, ho, wk * p->E_ref, rG);
-                }
-                dn += nn;
-                dg += nn;
+                const long long off = bounce ? (long long)(opposite(k) - k) * (long long)nn : (long long)to;
+                Store<S, R>::store2(dk + 2 * off, 0, fo, ho, wk * p->rho_ref, wk * p->E_ref, rN, rG);
+                dk += 2 * nn;
             };
             {
                 const R w0 = R(V::w(0));
-                emit(0, w0 * base0, w0 * dbase, ld_last(qn, 0, w0 * p->rho_ref), hv[0]);
-                qn += nn;
+                emit(0, w0 * base0, w0 * dbase, fv[0], hv[0]);
             }
 #pragma unroll
             for (int k = 1; k < Q; k += 2) {
@@ -430,11 +420,8 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false> struc
                 if (M::m(k) == 1) { cu += u[2]; cd += dv[2]; } else if (M::m(k) == -1) { cu -= u[2]; cd -= dv[2]; }
                 const R ev = wk * fma(R(4.5) * cu, cu, base0), od = (R(3) * wk) * cu;
                 const R dv_e = wk * fma(R(4.5) * cd, fma(R(2), cu, cd), dbase), dv_o = (R(3) * wk) * cd;
-                const R fa = ld_last(qn, 0, wk * p->rho_ref);
-                const R fb = ld_last(qn + nn, 0, wk * p->rho_ref);
-                qn += 2 * nn;
-                emit(k, ev + od, dv_e + dv_o, fa, hv[k]);
-                emit(k + 1, ev - od, dv_e - dv_o, fb, hv[k + 1]);
+                emit(k, ev + od, dv_e + dv_o, fv[k], hv[k]);
+                emit(k + 1, ev - od, dv_e - dv_o, fv[k + 1], hv[k + 1]);
             }
         };
         if (wall_lo || wall_hi || edge) collide(std::true_type{});
@@ -538,11 +525,19 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restr
     }
 }
 
+// CTAs per SM the single-domain step is compiled for (the register cap that
+// follows from it): D3Q19 keeps two 384-thread CTAs (80 registers) with FP32
+// and FP16 storage and one 512-thread CTA with FP64; D2Q9 keeps four (FP32)
+// or three 288-thread CTAs.
+template <int Q, typename S> struct FusedOcc {
+    static constexpr int kMinBlocks = Q == 19 ? (sizeof(S) == 8 ? 1 : 2) : (sizeof(S) == 4 ? 4 : 3);
+};
+
 // Single-domain fused step: CTA (x, y, z) takes tile (x TX, y TY) and the
 // z-th chunk of planes.  XW: instance for domains with walls on the
 // tile-plane axes (the other instance carries no trace of them).
 template <int Q, typename S, typename R, int TX, int TY, int NP, bool XW>
-__global__ void __launch_bounds__(TX* TY + NP) fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst,
+__global__ void __launch_bounds__(TX* TY + NP, FusedOcc<Q, S>::kMinBlocks) fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst,
                                                                  KParams<R> p, MarchGeom G, Counters* cnt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     fused_tile<Q, S, R, TX, TY, NP, false, false, XW>(src, dst, &p, G, p.step, blockIdx.x * TX, blockIdx.y * TY,
@@ -555,7 +550,7 @@ __global__ void __launch_bounds__(TX* TY + NP) fused_step_kernel(const S* __rest
 // the test hook lbm_test_drop_handoff set; the kernel above carries no trace
 // of it.
 template <int Q, typename S, typename R, int TX, int TY, int NP>
-__global__ void __launch_bounds__(TX* TY + NP) fused_step_fault_kernel(const S* __restrict__ src, S* __restrict__ dst,
+__global__ void __launch_bounds__(TX* TY + NP, FusedOcc<Q, S>::kMinBlocks) fused_step_fault_kernel(const S* __restrict__ src, S* __restrict__ dst,
                                                                        KParams<R> p, MarchGeom G, Counters* cnt,
                                                                        int fault_plane) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -6,9 +6,9 @@
 //                   pseudoforce for g, push streaming with walls (Eq. (lbe), (gk))
 // plus initialisation, output moments and the conservation reductions.
 //
-// Populations: one buffer of 2Q planes (N_0..N_{Q-1}, g_0..g_{Q-1}), each
-// plane nn = nx*ny*nz values, x fastest.  Fields: planes of nn values of the
-// arithmetic type R.
+// Populations: Q arrays of nn node pairs (N_k, g_k), nn = nx*ny*nz, x fastest
+// (lattice.cuh); checkpoints use 2Q set-major planes.  Fields: planes of nn
+// values of the arithmetic type R.
 #pragma once
 
 #include "lattice.cuh"
@@ -30,23 +30,51 @@ struct Counters {
 
 template <typename R> __device__ __forceinline__ bool finite_pos(R v) { return v > R(0) && isfinite(v); }
 
-// moments of one node from its 2Q populations, summed in fixed k order
-template <int Q, typename S, typename R>
+// moments of one node from its 2Q populations, each sum in fixed k order.
+// PAIRS: the library's pair layout; false: the set-major checkpoint layout.
+template <int Q, typename S, typename R, bool PAIRS = true>
 __device__ __forceinline__ void node_moments(const S* __restrict__ pop, long long nn, long long i,
                                              const KParams<R>& p, R& rho, R& jx, R& jy, R& jz, R& E) {
     using V = Vel<Q>;
     rho = R(0); jx = R(0); jy = R(0); jz = R(0); E = R(0);
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-        R f = Store<S, R>::load(pop, (size_t)k * nn + i, R(V::w(k)) * p.rho_ref);
+        const R sN = R(V::w(k)) * p.rho_ref, sG = R(V::w(k)) * p.E_ref;
+        R f, h;
+        if (PAIRS) {
+            Store<S, R>::load2(pop, pair_index(k, nn, i), sN, sG, f, h);
+        } else {
+            f = Store<S, R>::load(pop, (size_t)k * nn + i, sN);
+            h = Store<S, R>::load(pop, (size_t)(Q + k) * nn + i, sG);
+        }
         rho += f;
         if (V::cx(k) == 1) jx += f; else if (V::cx(k) == -1) jx -= f;
         if (V::cy(k) == 1) jy += f; else if (V::cy(k) == -1) jy -= f;
         if (V::D == 3) { if (V::cz(k) == 1) jz += f; else if (V::cz(k) == -1) jz -= f; }
+        E += h;
     }
-#pragma unroll
-    for (int k = 0; k < Q; ++k)
-        E += Store<S, R>::load(pop, (size_t)(Q + k) * nn + i, R(V::w(k)) * p.E_ref);
+}
+
+// Layout conversion between the 2Q set-major checkpoint planes and the pair
+// layout: element (s, k, n) moves between s Q nn + k nn + n and
+// 2 (k nn + n) + s.  W is an unsigned word of the storage element's size.
+template <typename W>
+__global__ void __launch_bounds__(256) sets_to_pairs_kernel(const W* __restrict__ sets, W* __restrict__ pairs,
+                                                            long long qnn) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < qnn; j += stride) {
+        pairs[2 * j] = sets[j];
+        pairs[2 * j + 1] = sets[qnn + j];
+    }
+}
+template <typename W>
+__global__ void __launch_bounds__(256) pairs_to_sets_kernel(const W* __restrict__ pairs, W* __restrict__ sets,
+                                                            long long qnn) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < qnn; j += stride) {
+        sets[j] = pairs[2 * j];
+        sets[qnn + j] = pairs[2 * j + 1];
+    }
 }
 
 // Step part 1: rho, u = j/rho, T = E/(rho c_v), Phi = sqrt(-(p - rho/3)).
@@ -161,10 +189,14 @@ __global__ void __launch_bounds__(256) collide_kernel(const S* __restrict__ src,
     if (p.conduction) dE += cond;
     if (p.latent != R(0)) dE += latent_heat(p, rho, T, div);
 
-    // energy of the node (same summation order as fields_kernel)
+    // the node's populations; its energy in the summation order of fields_kernel
+    R fv[Q], hv[Q];
     R E = R(0);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) E += Store<S, R>::load(src, (size_t)(Q + k) * nn + i, R(V::w(k)) * p.E_ref);
+    for (int k = 0; k < Q; ++k) {
+        Store<S, R>::load2(src, pair_index(k, nn, i), R(V::w(k)) * p.rho_ref, R(V::w(k)) * p.E_ref, fv[k], hv[k]);
+        E += hv[k];
+    }
     const R dEoverE = dE / E;
 
     const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
@@ -177,16 +209,15 @@ __global__ void __launch_bounds__(256) collide_kernel(const S* __restrict__ src,
         const R cd = cdot<Q, R>(k, du[0], du[1], du[2]);
         const R e0 = wk * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
         const R de = wk * (R(3) * cd + R(4.5) * cd * (R(2) * cu + cd) - R(1.5) * dsq);
-        const R f = Store<S, R>::load(src, (size_t)k * nn + i, wk * p.rho_ref);
-        const R h = Store<S, R>::load(src, (size_t)(Q + k) * nn + i, wk * p.E_ref);
+        const R f = fv[k], h = hv[k];
         const R fs = f + p.omega * (rho * e0 - f) + rho * de;
         R hs = h + p.omega_E * (E * e0 - h) + h * dEoverE;
         if (p.pseudoforce) hs += E * de;
         Nb m = neighbour<D>(x, y, z, V::cx(k), V::cy(k), V::cz(k), p);
         const int ko = m.ghost ? opposite(k) : k;
         const long long to = m.ghost ? i : m.n;
-        Store<S, R>::store(dst, (size_t)ko * nn + to, fs, R(V::w(ko)) * p.rho_ref, slot_bits(nbits, k));
-        Store<S, R>::store(dst, (size_t)(Q + ko) * nn + to, hs, R(V::w(ko)) * p.E_ref, slot_bits(nbits, Q + k));
+        Store<S, R>::store2(dst, pair_index(ko, nn, to), fs, hs, R(V::w(ko)) * p.rho_ref, R(V::w(ko)) * p.E_ref,
+                            slot_bits(nbits, k), slot_bits(nbits, Q + k));
     }
 }
 
@@ -224,8 +255,8 @@ __global__ void __launch_bounds__(256) init_kernel(S* __restrict__ pop, const do
         const R wk = R(V::w(k));
         const R cu = cdot<Q, R>(k, u[0], u[1], u[2]);
         const R e0 = wk * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
-        Store<S, R>::store(pop, (size_t)k * nn + i, rho * e0, wk * p.rho_ref, slot_bits(nbits, k));
-        Store<S, R>::store(pop, (size_t)(Q + k) * nn + i, E * e0, wk * p.E_ref, slot_bits(nbits, Q + k));
+        Store<S, R>::store2(pop, pair_index(k, nn, i), rho * e0, E * e0, wk * p.rho_ref, wk * p.E_ref,
+                            slot_bits(nbits, k), slot_bits(nbits, Q + k));
     }
 }
 
@@ -275,7 +306,9 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <int Q, typename S, typename R>
+// PAIRS: populations in the library's pair layout; false: set-major planes
+// (a checkpoint buffer, lbm_conservation_sums_noalloc)
+template <int Q, typename S, typename R, bool PAIRS = true>
 __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const S* __restrict__ pop, KParams<R> p,
                                                                 double* __restrict__ partials) {
     // Each thread sums the moments of its nodes (about nn / 262144 of them,
@@ -286,7 +319,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const S* __restr
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.nn; i += stride) {
         R rho, jx, jy, jz, E;
-        node_moments<Q, S, R>(pop, p.nn, i, p, rho, jx, jy, jz, E);
+        node_moments<Q, S, R, PAIRS>(pop, p.nn, i, p, rho, jx, jy, jz, E);
         acc[0].add((double)rho);
         acc[1].add((double)jx);
         acc[2].add((double)jy);

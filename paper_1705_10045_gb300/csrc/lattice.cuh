@@ -91,10 +91,24 @@ __device__ __forceinline__ unsigned slot_bits(unsigned nb, int slot) {
     return (nb * ((2u * (unsigned)slot + 1u) * 0x9E3779B9u)) >> 19;
 }
 
+// Population layout in device memory.  Every kernel reads a node's N_k and
+// g_k together (the moments need both sets, the collision updates both) and
+// the push sends both to the same neighbour, so the two sets are interleaved:
+// for each direction k an array of nn node pairs (N_k, g_k), x fastest.  The
+// value of set s (0: N, 1: g), direction k, node n is element
+// 2 (k nn + n) + s, and pair index k nn + n moves both in one vector access.
+// Checkpoints (lbm_get_state / lbm_set_state) use the set-major layout of 2Q
+// planes (N_0..N_{Q-1}, g_0..g_{Q-1}); the conversion kernels sit in
+// kernels.cuh.
+__host__ __device__ __forceinline__ size_t pair_index(int k, long long nn, long long n) {
+    return (size_t)k * (size_t)nn + (size_t)n;
+}
+
 template <typename S, typename R> struct Store;
 // load_last: the same load for the last use of a value on this SM (the fused
 // step's consumer reload); L1::no_allocate leaves L1 to the lines the moment
-// stage will still reuse.
+// stage will still reuse.  load2 / store2: the pair (N_k, g_k) at pair index
+// i (shifts sN, sG; random bits rN, rG of the FP16 rounding), one access.
 
 template <> struct Store<double, double> {
     static constexpr bool kStochastic = false;
@@ -117,6 +131,25 @@ template <> struct Store<double, double> {
         asm volatile("ld.global.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p + i) : "memory");
         return v;
     }
+    __device__ static void load2(const double* p, size_t i, double, double, double& a, double& b) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p) + i);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static void load2_last(const double* p, size_t i, double, double, double& a, double& b) {
+        asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p + 2 * i));
+    }
+    __device__ static void load2_coh(const double* p, size_t i, double, double, double& a, double& b) {
+        asm volatile("ld.global.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p + 2 * i) : "memory");
+    }
+    __device__ static void load2_last_coh(const double* p, size_t i, double, double, double& a, double& b) {
+        asm volatile("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p + 2 * i)
+                     : "memory");
+    }
+    __device__ static void store2(double* p, size_t i, double a, double b, double, double, unsigned = 0,
+                                  unsigned = 0) {
+        reinterpret_cast<double2*>(p)[i] = make_double2(a, b);
+    }
 };
 
 template <> struct Store<float, float> {
@@ -137,6 +170,24 @@ template <> struct Store<float, float> {
         float v;
         asm volatile("ld.global.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p + i) : "memory");
         return v;
+    }
+    __device__ static void load2(const float* p, size_t i, float, float, float& a, float& b) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static void load2_last(const float* p, size_t i, float, float, float& a, float& b) {
+        asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "l"(p + 2 * i));
+    }
+    __device__ static void load2_coh(const float* p, size_t i, float, float, float& a, float& b) {
+        asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "l"(p + 2 * i) : "memory");
+    }
+    __device__ static void load2_last_coh(const float* p, size_t i, float, float, float& a, float& b) {
+        asm volatile("ld.global.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "l"(p + 2 * i)
+                     : "memory");
+    }
+    __device__ static void store2(float* p, size_t i, float a, float b, float, float, unsigned = 0, unsigned = 0) {
+        reinterpret_cast<float2*>(p)[i] = make_float2(a, b);
     }
 };
 
@@ -163,10 +214,40 @@ template <> struct Store<__half, float> {
     // rnd13: 13 random bits; adding them below the 10 FP16 mantissa bits of
     // the FP32 value and truncating rounds the magnitude up with probability
     // equal to the discarded fraction (unbiased for FP16-normal values)
-    __device__ static void store(__half* p, size_t i, float v, float shift, unsigned rnd13 = 0) {
+    __device__ static unsigned short round(float v, float shift, unsigned rnd13) {
         unsigned b = __float_as_uint(v - shift);
         b = (b + (rnd13 & 0x1FFFu)) & ~0x1FFFu;
-        p[i] = __float2half_rz(__uint_as_float(b));
+        return __half_as_ushort(__float2half_rz(__uint_as_float(b)));
+    }
+    __device__ static void store(__half* p, size_t i, float v, float shift, unsigned rnd13 = 0) {
+        p[i] = __ushort_as_half(round(v, shift, rnd13));
+    }
+    // a pair is one 32-bit word: N_k in the low half, g_k in the high half
+    __device__ static void unpack(unsigned w, float sN, float sG, float& a, float& b) {
+        a = __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))) + sN;
+        b = __half2float(__ushort_as_half((unsigned short)(w >> 16))) + sG;
+    }
+    __device__ static void load2(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
+        unpack(__ldg(reinterpret_cast<const unsigned*>(p) + i), sN, sG, a, b);
+    }
+    __device__ static void load2_last(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
+        unsigned w;
+        asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(w) : "l"(p + 2 * i));
+        unpack(w, sN, sG, a, b);
+    }
+    __device__ static void load2_coh(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
+        unsigned w;
+        asm volatile("ld.global.b32 %0, [%1];" : "=r"(w) : "l"(p + 2 * i) : "memory");
+        unpack(w, sN, sG, a, b);
+    }
+    __device__ static void load2_last_coh(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
+        unsigned w;
+        asm volatile("ld.global.L1::no_allocate.b32 %0, [%1];" : "=r"(w) : "l"(p + 2 * i) : "memory");
+        unpack(w, sN, sG, a, b);
+    }
+    __device__ static void store2(__half* p, size_t i, float a, float b, float sN, float sG, unsigned rN = 0,
+                                  unsigned rG = 0) {
+        reinterpret_cast<unsigned*>(p)[i] = (unsigned)round(a, sN, rN) | ((unsigned)round(b, sG, rG) << 16);
     }
 };
 

@@ -38,6 +38,39 @@ using lbm::set_error;
 namespace {
 
 constexpr uint32_t kStateMagic = 0x314d424cu;   // "LBM1"
+
+// Convert the Q nn population pairs of `from` (to_pairs: 2Q set-major planes
+// of `from`) into the other layout in `to`; elem is the storage element size.
+int convert_layout(const void* from, void* to, long long qnn, size_t elem, bool to_pairs, cudaStream_t stream) {
+    long long blocks = (qnn + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    const unsigned g = (unsigned)(blocks > 0 ? blocks : 1);
+    switch (elem) {
+        case 8:
+            if (to_pairs)
+                lbm::sets_to_pairs_kernel<<<g, 256, 0, stream>>>((const unsigned long long*)from,
+                                                                (unsigned long long*)to, qnn);
+            else
+                lbm::pairs_to_sets_kernel<<<g, 256, 0, stream>>>((const unsigned long long*)from,
+                                                                (unsigned long long*)to, qnn);
+            break;
+        case 4:
+            if (to_pairs)
+                lbm::sets_to_pairs_kernel<<<g, 256, 0, stream>>>((const unsigned*)from, (unsigned*)to, qnn);
+            else
+                lbm::pairs_to_sets_kernel<<<g, 256, 0, stream>>>((const unsigned*)from, (unsigned*)to, qnn);
+            break;
+        default:
+            if (to_pairs)
+                lbm::sets_to_pairs_kernel<<<g, 256, 0, stream>>>((const unsigned short*)from, (unsigned short*)to,
+                                                                qnn);
+            else
+                lbm::pairs_to_sets_kernel<<<g, 256, 0, stream>>>((const unsigned short*)from, (unsigned short*)to,
+                                                                qnn);
+            break;
+    }
+    return cuda_error(cudaGetLastError(), "layout conversion launch");
+}
 constexpr size_t kStateHeader = 16;
 
 struct DeviceGuard {
@@ -434,8 +467,12 @@ int lbm_get_state(lbm_handle* h, void* buf, int mem) {
     const cudaMemcpyKind k_d = mem == LBM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     int rc;
     if ((rc = cuda_error(cudaMemcpyAsync(buf, hdr, kStateHeader, k_h, h->stream), "state copy"))) return rc;
-    if ((rc = cuda_error(cudaMemcpyAsync((unsigned char*)buf + kStateHeader, h->pop[h->cur],
-                                         lbm_state_bytes(h) - kStateHeader, k_d, h->stream),
+    // set-major planes, formed in the idle population buffer (the next step
+    // overwrites all of it)
+    void* idle = h->pop[h->cur ^ 1];
+    if ((rc = convert_layout(h->pop[h->cur], idle, (long long)h->Q * h->nn, h->elem, false, h->stream))) return rc;
+    if ((rc = cuda_error(cudaMemcpyAsync((unsigned char*)buf + kStateHeader, idle, lbm_state_bytes(h) - kStateHeader,
+                                         k_d, h->stream),
                          "state copy")))
         return rc;
     return sync_and_latch(h);
@@ -466,12 +503,14 @@ int lbm_set_state(lbm_handle* h, const void* buf, int mem) {
         set_error("lbm_set_state: buffer does not hold a state of this lattice and storage format");
         return LBM_ERR_INVALID_ARG;
     }
-    if ((rc = cuda_error(cudaMemcpyAsync(h->pop[h->cur], (const unsigned char*)buf + kStateHeader,
+    void* idle = h->pop[h->cur ^ 1];
+    if ((rc = cuda_error(cudaMemcpyAsync(idle, (const unsigned char*)buf + kStateHeader,
                                          lbm_state_bytes(h) - kStateHeader,
                                          mem == LBM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                                          h->stream),
                          "state copy")))
         return rc;
+    if ((rc = convert_layout(idle, h->pop[h->cur], (long long)h->Q * h->nn, h->elem, true, h->stream))) return rc;
     if ((rc = cuda_error(cudaMemsetAsync(h->cnt, 0, sizeof(lbm::Counters), h->stream), "counter reset"))) return rc;
     if ((rc = cuda_error(cudaStreamSynchronize(h->stream), "stream synchronize"))) return rc;
     h->reported_bad = 0;

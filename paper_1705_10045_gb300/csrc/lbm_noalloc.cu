@@ -64,7 +64,9 @@ int launch_sums(int nx, int ny, int nz, double rho_ref, double E_ref, const void
     kp.nn = (long long)nx * ny * nz;
     kp.rho_ref = (R)rho_ref;
     kp.E_ref = (R)E_ref;
-    lbm::reduce_kernel<Q, S, R><<<lbm::kReduceBlocks, lbm::kReduceThreads, 0, stream>>>((const S*)pop, kp, scratch);
+    // the caller's buffer holds set-major planes (the checkpoint layout)
+    lbm::reduce_kernel<Q, S, R, false>
+        <<<lbm::kReduceBlocks, lbm::kReduceThreads, 0, stream>>>((const S*)pop, kp, scratch);
     lbm::reduce_final_kernel<<<1, 32, 0, stream>>>(scratch, lbm::kReduceBlocks, sums);
     return lbm::cuda_error(cudaGetLastError(), "lbm_conservation_sums_noalloc launch");
 }

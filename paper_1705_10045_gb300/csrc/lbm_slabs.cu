@@ -99,12 +99,13 @@ int copy_rows(const void* src, long long spitch, void* dst, long long dpitch, lo
 }
 
 // planes [first, first + count) of every population array of the current state
+// (Q arrays of node pairs (N_k, g_k), 2 elem bytes per node)
 int copy_planes(lbm_handle* dst, int dst_first, const lbm_handle* src, int src_first, int count) {
     const long long plane = plane_nodes(src->p);
-    const long long e = (long long)src->elem;
+    const long long e = 2 * (long long)src->elem;
     const auto* s = static_cast<const unsigned char*>(src->pop[src->cur]) + src_first * plane * e;
     auto* d = static_cast<unsigned char*>(dst->pop[dst->cur]) + dst_first * plane * e;
-    return copy_rows(s, src->nn * e, d, dst->nn * e, count * plane * e, 2 * src->Q, dst->stream);
+    return copy_rows(s, src->nn * e, d, dst->nn * e, count * plane * e, src->Q, dst->stream);
 }
 
 // Conservation sums of nodes [i0, i0 + n) of a population buffer whose
@@ -502,10 +503,10 @@ int lbm_get_planes(lbm_handle* h, int first, int count, void* buf, int mem) {
         return LBM_ERR_INVALID_ARG;
     }
     DeviceGuard dg(h->p.device);
-    const long long e = (long long)h->elem, width = count * plane_nodes(h->p) * e;
+    const long long e = 2 * (long long)h->elem, width = count * plane_nodes(h->p) * e;
     const auto* src = static_cast<const unsigned char*>(h->pop[h->cur]) + first * plane_nodes(h->p) * e;
-    if (mem == LBM_MEM_DEVICE) return copy_rows(src, h->nn * e, buf, width, width, 2 * h->Q, h->stream);
-    for (int r = 0; r < 2 * h->Q; ++r)
+    if (mem == LBM_MEM_DEVICE) return copy_rows(src, h->nn * e, buf, width, width, h->Q, h->stream);
+    for (int r = 0; r < h->Q; ++r)
         if (int rc = cuda_error(cudaMemcpyAsync(static_cast<unsigned char*>(buf) + r * width, src + r * h->nn * e,
                                                 (size_t)width, cudaMemcpyDeviceToHost, h->stream),
                                 "plane copy"))
@@ -524,10 +525,10 @@ int lbm_set_planes(lbm_handle* h, int first, int count, const void* buf, int mem
         return LBM_ERR_INVALID_ARG;
     }
     DeviceGuard dg(h->p.device);
-    const long long e = (long long)h->elem, width = count * plane_nodes(h->p) * e;
+    const long long e = 2 * (long long)h->elem, width = count * plane_nodes(h->p) * e;
     auto* dst = static_cast<unsigned char*>(h->pop[h->cur]) + first * plane_nodes(h->p) * e;
-    if (mem == LBM_MEM_DEVICE) return copy_rows(buf, width, dst, h->nn * e, width, 2 * h->Q, h->stream);
-    for (int r = 0; r < 2 * h->Q; ++r)
+    if (mem == LBM_MEM_DEVICE) return copy_rows(buf, width, dst, h->nn * e, width, h->Q, h->stream);
+    for (int r = 0; r < h->Q; ++r)
         if (int rc = cuda_error(cudaMemcpyAsync(dst + r * h->nn * e, static_cast<const unsigned char*>(buf) + r * width,
                                                 (size_t)width, cudaMemcpyHostToDevice, h->stream),
                                 "plane copy"))

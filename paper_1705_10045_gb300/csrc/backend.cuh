@@ -46,10 +46,12 @@ inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + thre
 // SM) in FP32/FP16 and 256 producers in FP64.  D2Q9 uses rows of 128 nodes
 // with 160 producers: one producer per node of the 132-node ring row, so the
 // moments of a row take a single round of loads.
+// SPLIT: the consumers form the moments of their own nodes and the producers
+// only those of the ring's border (fused_tile)
 template <int Q, typename R> struct FusedTile;
-template <typename R> struct FusedTile<9, R> { static constexpr int TX = 128, TY = 1, NP = 160; };
-template <> struct FusedTile<19, float> { static constexpr int TX = 32, TY = 8, NP = 128; };
-template <> struct FusedTile<19, double> { static constexpr int TX = 32, TY = 8, NP = 256; };
+template <typename R> struct FusedTile<9, R> { static constexpr int TX = 128, TY = 1, NP = 160; static constexpr bool SPLIT = false; };
+template <> struct FusedTile<19, float> { static constexpr int TX = 32, TY = 8, NP = 128; static constexpr bool SPLIT = true; };
+template <> struct FusedTile<19, double> { static constexpr int TX = 32, TY = 8, NP = 256; static constexpr bool SPLIT = true; };
 
 // CTA shapes a batch may run with (TX x TY consumers + NP producers); the
 // autotuner times each on the batch and keeps the fastest.
@@ -64,6 +66,7 @@ template <typename R> struct BatchShape<19, R, 2> { static constexpr int TX = 32
 
 template <int Q, typename S, typename R> struct Impl {
     static constexpr int TX = FusedTile<Q, R>::TX, TY = FusedTile<Q, R>::TY, NP = FusedTile<Q, R>::NP;
+    static constexpr bool SPLIT = FusedTile<Q, R>::SPLIT;
     static int launches(const lbm_handle* h) { return h->p.step_kernel == LBM_STEP_THREE_LAUNCH ? 3 : 1; }
 
     static MarchGeom geometry(const lbm_handle* h) {
@@ -82,16 +85,17 @@ template <int Q, typename S, typename R> struct Impl {
 
     static void launch_fused(lbm_handle* h, const KParams<R>& kp) {
         const MarchGeom G = geometry(h);
-        const size_t smem = FusedShape<TX, TY>::template smem_bytes<R>();
+        const size_t smem = FusedShape<TX, TY, SPLIT>::template smem_bytes<R>();
         const bool xw = h->p.wall_x || (Q == 19 && h->p.wall_y);
-        auto kern = xw ? fused_step_kernel<Q, S, R, TX, TY, NP, true> : fused_step_kernel<Q, S, R, TX, TY, NP, false>;
+        auto kern = xw ? fused_step_kernel<Q, S, R, TX, TY, NP, true, SPLIT>
+                       : fused_step_kernel<Q, S, R, TX, TY, NP, false, SPLIT>;
         if (!h->fused_ready) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             h->fused_ready = true;
         }
         const dim3 grid((G.na + TX - 1) / TX, (G.nb + TY - 1) / TY, (G.nm + G.chunk - 1) / G.chunk);
         if (h->fault_drop > 0) {   // fault-injection test hook (lbm_test_drop_handoff)
-            auto fk = fused_step_fault_kernel<Q, S, R, TX, TY, NP>;
+            auto fk = fused_step_fault_kernel<Q, S, R, TX, TY, NP, SPLIT>;
             cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             fk<<<grid, TX * TY + NP, smem, h->stream>>>((const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], kp, G,
                                                         (Counters*)h->cnt, h->fault_drop - 1);

@@ -107,8 +107,10 @@ struct MarchGeom {
 };
 
 // Plane buffers: Phi for 3 planes, rho/u/T for 5 planes, du for 4 planes
-// (the consumer trails the producer by three planes).
-template <int TX, int TY> struct FusedShape {
+// (the consumer trails the producer by three planes).  SPLIT: the consumers
+// form the moments of their own nodes three planes ahead, which takes one
+// more rho/u/T plane and a third mbarrier ring.
+template <int TX, int TY, bool SPLIT = false> struct FusedShape {
     static constexpr int RB = TY > 1 ? 2 : 0;           // ring width across b (none for D2Q9)
     static constexpr int RW = TX + 4;                   // 2-ring region (Phi)
     static constexpr int RH = TY + 2 * RB;
@@ -118,17 +120,30 @@ template <int TX, int TY> struct FusedShape {
     static constexpr int FH = TY + 2 * FB;
     static constexpr int F = FW * FH;
     static constexpr int kRut = 5;                      // rho, ua, ub, um, T
-    static constexpr int kPhiSlots = 3, kRutSlots = 5, kDuSlots = 4;
+    static constexpr int kPhiSlots = 3, kRutSlots = SPLIT ? 6 : 5, kDuSlots = 4;
     static constexpr int kHandSlots = 8;   // mbarrier ring of the producer/consumer hand-off
+    static constexpr int kRings = SPLIT ? 3 : 2;
+    // ring nodes outside the tile: RB full rows above and below, 2 columns
+    // left and right of each tile row
+    static constexpr int kBorder = 2 * RB * RW + 4 * TY;
     template <typename R_> static constexpr size_t table_offset() {
         return sizeof(R_) * ((size_t)kPhiSlots * R + (size_t)kRutSlots * kRut * F + (size_t)kDuSlots * 3 * F);
     }
     template <typename R_> static constexpr size_t barrier_offset() {
         return (table_offset<R_>() + sizeof(int) * (RW + RH) + 7) & ~(size_t)7;
     }
-    // plane buffers, ring tables, 2 x kHandSlots mbarriers and an abort flag
+    // plane buffers, ring tables, kRings x kHandSlots mbarriers and an abort flag
     template <typename R_> static constexpr size_t smem_bytes() {
-        return barrier_offset<R_>() + 8 * (2 * kHandSlots + 1);
+        return barrier_offset<R_>() + 8 * (kRings * kHandSlots + 1);
+    }
+    // ring index of border node q < kBorder
+    __device__ static int border_ring(int q) {
+        if (q < 2 * RB * RW) {
+            const int row = q / RW;
+            return (row < RB ? row : row + TY) * RW + q % RW;
+        }
+        const int q2 = q - 2 * RB * RW, c = q2 & 3;
+        return (RB + (q2 >> 2)) * RW + (c < 2 ? c : c + TX);
     }
 };
 
@@ -161,10 +176,10 @@ __device__ __forceinline__ int wall_edges(const KParams<R>& p, int Q, int ga, in
 
 // COH: read the populations through coherent loads (the persistent batch
 // kernel reads, in one launch, buffers that other CTAs wrote earlier in it).
-template <int Q, typename S, typename R, int TX, int TY, bool COH = false> struct FusedStages {
+template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool SPLIT = false> struct FusedStages {
     using V = Vel<Q>;
     using M = MVel<Q>;
-    using Sh = FusedShape<TX, TY>;
+    using Sh = FusedShape<TX, TY, SPLIT>;
     static constexpr int RB = Sh::RB, RW = Sh::RW, RH = Sh::RH, R_ = Sh::R, FW = Sh::FW, FB = Sh::FB, F_ = Sh::F;
 
     R* phis;     // [kPhiSlots][R_]
@@ -204,8 +219,22 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false> struc
     __device__ void m_stage(int m, int t, int nt) const {
         const int plane_off = wrapi(m, G.nm) * plane_n;
         const int sp = slotn(m, Sh::kPhiSlots), sr = slotn(m, Sh::kRutSlots);
+        for (int r = t; r < R_; r += nt) m_node(plane_off, sp, sr, r);
+    }
+    // the same for the border nodes only (SPLIT: the consumers take the tile)
+    __device__ void m_border(int m, int t, int nt) const {
+        const int plane_off = wrapi(m, G.nm) * plane_n;
+        const int sp = slotn(m, Sh::kPhiSlots), sr = slotn(m, Sh::kRutSlots);
+        for (int q = t; q < Sh::kBorder; q += nt) m_node(plane_off, sp, sr, Sh::border_ring(q));
+    }
+    // the moments of tile node (ta, tb) of plane m
+    __device__ void m_interior(int m, int ta, int tb) const {
+        m_node(wrapi(m, G.nm) * plane_n, slotn(m, Sh::kPhiSlots), slotn(m, Sh::kRutSlots), (tb + RB) * RW + ta + 2);
+    }
+    // Phi of ring node r, and rho, u, T if r lies in the 1-ring region
+    __device__ __forceinline__ void m_node(int plane_off, int sp, int sr, int r) const {
         const R third = R(1.0 / 3.0);
-        for (int r = t; r < R_; r += nt) {
+        {
             const int ra = r % RW, rb = r / RW;
             const size_t n = (size_t)(plane_off + ring_b[rb] + ring_a[ra]);
             R fN[Q], fG[Q];
@@ -435,11 +464,11 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false> struc
 // FAULT instantiates the fault-injection form: the first CTA withholds the
 // hand-off of plane fault_plane (tests of the bounded waits only).
 template <int Q, typename S, typename R, int TX, int TY, int NP, bool FAULT = false, bool COH = false,
-          bool XW = true>
+          bool XW = true, bool SPLIT = false>
 __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restrict__ dst, const KParams<R>* p,
                                            const MarchGeom& G, unsigned step, int a0, int b0, int zb,
                                            Counters* cnt, unsigned char* smem_raw, int fault_plane = -1) {
-    using St = FusedStages<Q, S, R, TX, TY, COH>;
+    using St = FusedStages<Q, S, R, TX, TY, COH, SPLIT>;
     using Sh = typename St::Sh;
     constexpr int NC = TX * TY, NT = NC + NP;
     St st;
@@ -469,15 +498,22 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restr
     // the wait parity is (u / D) & 1; neither side gets two phases ahead of
     // the other's wait (producers run at most 2 iterations ahead of the plane
     // they need released, consumers cannot pass the producers).
+    // SPLIT adds mint[s]: every consumer has formed the moments of its node of
+    // plane c + 3 (u = c - zb), which the producers' F stage of iteration
+    // c + 3 reads.  A consumer forms them right after its wait for iteration
+    // c + 2, into buffer slots whose last readers (F(c+1), C(c-2)) that wait
+    // has ordered before it; the producers wait on every phase in order.
     constexpr int D = Sh::kHandSlots;
     unsigned long long* full = reinterpret_cast<unsigned long long*>(smem_raw + Sh::template barrier_offset<R>());
     unsigned long long* empty = full + D;
-    volatile int* aborted = reinterpret_cast<volatile int*>(empty + D);
+    unsigned long long* mint = empty + D;
+    volatile int* aborted = reinterpret_cast<volatile int*>(full + Sh::kRings * D);
     if (tid == 0) {
         *aborted = 0;
         for (int s = 0; s < D; ++s) {
             mbar_init(full + s, 1);
             mbar_init(empty + s, NC);
+            if (SPLIT) mbar_init(mint + s, NC);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -493,12 +529,19 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restr
     if (tid >= NC) {
         // producers: iteration i builds M(i) and F(i-1).  M(i) and F(i-1)
         // overwrite the buffers that C(i-4) read last.
+        // SPLIT: from plane zb + 3 on the consumers form the tile's moments
+        // and the producers the border's.
         const int t = tid - NC;
         for (int i = zb - 2; i < ze + 3; ++i) {
             const int cw = i - 4;
             if (cw >= zb && cw < ze) wait(empty, cw - zb);
             const bool m_need = i <= ze + 1 && (walls ? (i >= 0 && i < G.nm) : true);
-            if (m_need) st.m_stage(i, t, NP);
+            const bool split = SPLIT && i >= zb + 3 && i <= ze + 1;
+            if (m_need) {
+                if (split) st.m_border(i, t, NP);
+                else st.m_stage(i, t, NP);
+            }
+            if (split) wait(mint, i - zb - 3);
             asm volatile("bar.sync 1, %0;" ::"r"(NP));
             const int f = i - 1;
             const bool f_need = f >= zb - 1 && f <= ze && (walls ? (f >= 0 && f < G.nm) : true);
@@ -519,6 +562,11 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restr
         const int edge = XW ? wall_edges(*p, Q, ga, gb, G.na, G.nb) : 0;
         for (int c = zb; c < ze; ++c) {
             wait(full, c - zb + 4);
+            if (SPLIT && c + 3 <= ze + 1) {
+                const int m = c + 3;
+                if (walls ? m < G.nm : true) st.m_interior(m, ta, tb);
+                mbar_arrive(mint + ((c - zb) % D));
+            }
             if (owns) st.template c_stage<XW>(c, ta, tb, n_ab, dA_m, dA_p, dB_m, dB_p, edge, cnt);
             mbar_arrive(empty + ((c - zb) % D));
         }
@@ -535,13 +583,14 @@ template <int Q, typename S> struct FusedOcc {
 
 // Single-domain fused step: CTA (x, y, z) takes tile (x TX, y TY) and the
 // z-th chunk of planes.  XW: instance for domains with walls on the
-// tile-plane axes (the other instance carries no trace of them).
-template <int Q, typename S, typename R, int TX, int TY, int NP, bool XW>
-__global__ void __launch_bounds__(TX* TY + NP, FusedOcc<Q, S>::kMinBlocks) fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst,
-                                                                 KParams<R> p, MarchGeom G, Counters* cnt) {
+// tile-plane axes (the other instance carries no trace of them).  SPLIT: the
+// consumers form their own nodes' moments (fused_tile).
+template <int Q, typename S, typename R, int TX, int TY, int NP, bool XW, bool SPLIT>
+__global__ void __launch_bounds__(TX* TY + NP, FusedOcc<Q, S>::kMinBlocks)
+    fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst, KParams<R> p, MarchGeom G, Counters* cnt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_tile<Q, S, R, TX, TY, NP, false, false, XW>(src, dst, &p, G, p.step, blockIdx.x * TX, blockIdx.y * TY,
-                                                      blockIdx.z * G.chunk, cnt, smem_raw);
+    fused_tile<Q, S, R, TX, TY, NP, false, false, XW, SPLIT>(src, dst, &p, G, p.step, blockIdx.x * TX,
+                                                             blockIdx.y * TY, blockIdx.z * G.chunk, cnt, smem_raw);
 }
 
 // The same step with the fault-injection hook: the first CTA withholds the
@@ -549,13 +598,14 @@ __global__ void __launch_bounds__(TX* TY + NP, FusedOcc<Q, S>::kMinBlocks) fused
 // and the timeout is counted.  Launched only for handles created with
 // the test hook lbm_test_drop_handoff set; the kernel above carries no trace
 // of it.
-template <int Q, typename S, typename R, int TX, int TY, int NP>
-__global__ void __launch_bounds__(TX* TY + NP, FusedOcc<Q, S>::kMinBlocks) fused_step_fault_kernel(const S* __restrict__ src, S* __restrict__ dst,
-                                                                       KParams<R> p, MarchGeom G, Counters* cnt,
-                                                                       int fault_plane) {
+template <int Q, typename S, typename R, int TX, int TY, int NP, bool SPLIT>
+__global__ void __launch_bounds__(TX* TY + NP, FusedOcc<Q, S>::kMinBlocks)
+    fused_step_fault_kernel(const S* __restrict__ src, S* __restrict__ dst, KParams<R> p, MarchGeom G, Counters* cnt,
+                            int fault_plane) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_tile<Q, S, R, TX, TY, NP, true>(src, dst, &p, G, p.step, blockIdx.x * TX, blockIdx.y * TY,
-                                          blockIdx.z * G.chunk, cnt, smem_raw, fault_plane);
+    fused_tile<Q, S, R, TX, TY, NP, true, false, true, SPLIT>(src, dst, &p, G, p.step, blockIdx.x * TX,
+                                                              blockIdx.y * TY, blockIdx.z * G.chunk, cnt, smem_raw,
+                                                              fault_plane);
 }
 
 // ---------------------------------------------------------------------------

@@ -56,13 +56,15 @@ template <> struct FusedTile<19, double> { static constexpr int TX = 32, TY = 8,
 // CTA shapes a batch may run with (TX x TY consumers + NP producers); the
 // autotuner times each on the batch and keeps the fastest.
 // MB: CTAs per SM the batch kernel is compiled for (its register cap).
+// SPLIT: as for the single-domain step (D3Q19: consumers form their own
+// nodes' moments).
 template <int Q, typename R, int V> struct BatchShape;
-template <typename R> struct BatchShape<9, R, 0> { static constexpr int TX = 128, TY = 1, NP = 160, MB = 3; };
-template <typename R> struct BatchShape<9, R, 1> { static constexpr int TX = 32, TY = 1, NP = 32, MB = 16; };
-template <typename R> struct BatchShape<9, R, 2> { static constexpr int TX = 64, TY = 1, NP = 64, MB = 8; };
-template <typename R> struct BatchShape<19, R, 0> { static constexpr int TX = 32, TY = 8, NP = 128, MB = 2; };
-template <typename R> struct BatchShape<19, R, 1> { static constexpr int TX = 32, TY = 8, NP = 160, MB = 2; };
-template <typename R> struct BatchShape<19, R, 2> { static constexpr int TX = 32, TY = 4, NP = 96, MB = 3; };
+template <typename R> struct BatchShape<9, R, 0> { static constexpr int TX = 128, TY = 1, NP = 160, MB = 3; static constexpr bool SPLIT = false; };
+template <typename R> struct BatchShape<9, R, 1> { static constexpr int TX = 32, TY = 1, NP = 32, MB = 16; static constexpr bool SPLIT = false; };
+template <typename R> struct BatchShape<9, R, 2> { static constexpr int TX = 64, TY = 1, NP = 64, MB = 8; static constexpr bool SPLIT = false; };
+template <typename R> struct BatchShape<19, R, 0> { static constexpr int TX = 32, TY = 8, NP = 128, MB = 2; static constexpr bool SPLIT = true; };
+template <typename R> struct BatchShape<19, R, 1> { static constexpr int TX = 32, TY = 8, NP = 160, MB = 2; static constexpr bool SPLIT = true; };
+template <typename R> struct BatchShape<19, R, 2> { static constexpr int TX = 32, TY = 4, NP = 96, MB = 3; static constexpr bool SPLIT = true; };
 
 template <int Q, typename S, typename R> struct Impl {
     static constexpr int TX = FusedTile<Q, R>::TX, TY = FusedTile<Q, R>::TY, NP = FusedTile<Q, R>::NP;
@@ -201,7 +203,7 @@ template <int Q, typename S, typename R> struct Impl {
         return G;
     }
 
-    template <int BTX, int BTY, int BNP, int BMB>
+    template <int BTX, int BTY, int BNP, int BMB, bool BSP>
     static int build_shape(lbm_batch* b) {
         std::vector<BatchItem> items;
         DomainDesc<R>* descs = (DomainDesc<R>*)b->h_descs;
@@ -238,12 +240,12 @@ template <int Q, typename S, typename R> struct Impl {
                                                     cudaMemcpyHostToDevice, b->stream), "batch table copy"))
                 return rc;
         // one persistent CTA per resident slot: occupancy times the SM count
-        const size_t smem = FusedShape<BTX, BTY>::template smem_bytes<R>();
+        const size_t smem = FusedShape<BTX, BTY, BSP>::template smem_bytes<R>();
         b->xw = false;
         for (auto* h : b->doms) b->xw = b->xw || (h && (h->p.wall_x || (Q == 19 && h->p.wall_y)));
-        const void* kerns[3] = {(const void*)fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, true, true>,
-                                (const void*)fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, true>,
-                                (const void*)fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, false>};
+        const void* kerns[3] = {(const void*)fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, true, true, BSP>,
+                                (const void*)fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, true, BSP>,
+                                (const void*)fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, false, BSP>};
         for (const void* kern : kerns)
             if (int rc = cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                                     "batch kernel attribute"))
@@ -261,22 +263,22 @@ template <int Q, typename S, typename R> struct Impl {
     }
 
     // the persistent launch of a request (steps and scheduling state already in device memory)
-    template <int BTX, int BTY, int BNP, int BMB>
+    template <int BTX, int BTY, int BNP, int BMB, bool BSP>
     static void launch_shape(lbm_batch* b) {
-        const size_t smem = FusedShape<BTX, BTY>::template smem_bytes<R>();
+        const size_t smem = FusedShape<BTX, BTY, BSP>::template smem_bytes<R>();
         const int n_doms = (int)b->doms.size();
         const int grid = std::max(1, b->grid);   // CTAs beyond the work of a request leave at once
         const auto* items = (const BatchItem*)b->d_items;
         const auto* descs = (const DomainDesc<R>*)b->d_descs;
         auto* sched = (BatchSched*)b->d_sched;
         if (b->fault_item >= 0)
-            fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, true, true><<<grid, BTX * BTY + BNP, smem, b->stream>>>(
+            fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, true, true, BSP><<<grid, BTX * BTY + BNP, smem, b->stream>>>(
                 items, descs, b->n_items, sched, n_doms, b->fault_item);
         else if (b->xw)
-            fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, true><<<grid, BTX * BTY + BNP, smem, b->stream>>>(
+            fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, true, BSP><<<grid, BTX * BTY + BNP, smem, b->stream>>>(
                 items, descs, b->n_items, sched, n_doms, -1);
         else
-            fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, false><<<grid, BTX * BTY + BNP, smem, b->stream>>>(
+            fused_batch_kernel<Q, S, R, BTX, BTY, BNP, BMB, false, false, BSP><<<grid, BTX * BTY + BNP, smem, b->stream>>>(
                 items, descs, b->n_items, sched, n_doms, -1);
     }
 
@@ -294,9 +296,9 @@ template <int Q, typename S, typename R> struct Impl {
 
 template <int Q, typename S, typename R> int Impl<Q, S, R>::batch_build(lbm_batch* b) {
     switch (b->variant) {
-        case 0: return build_shape<BatchShape<Q, R, 0>::TX, BatchShape<Q, R, 0>::TY, BatchShape<Q, R, 0>::NP, BatchShape<Q, R, 0>::MB>(b);
-        case 1: return build_shape<BatchShape<Q, R, 1>::TX, BatchShape<Q, R, 1>::TY, BatchShape<Q, R, 1>::NP, BatchShape<Q, R, 1>::MB>(b);
-        default: return build_shape<BatchShape<Q, R, 2>::TX, BatchShape<Q, R, 2>::TY, BatchShape<Q, R, 2>::NP, BatchShape<Q, R, 2>::MB>(b);
+        case 0: return build_shape<BatchShape<Q, R, 0>::TX, BatchShape<Q, R, 0>::TY, BatchShape<Q, R, 0>::NP, BatchShape<Q, R, 0>::MB, BatchShape<Q, R, 0>::SPLIT>(b);
+        case 1: return build_shape<BatchShape<Q, R, 1>::TX, BatchShape<Q, R, 1>::TY, BatchShape<Q, R, 1>::NP, BatchShape<Q, R, 1>::MB, BatchShape<Q, R, 1>::SPLIT>(b);
+        default: return build_shape<BatchShape<Q, R, 2>::TX, BatchShape<Q, R, 2>::TY, BatchShape<Q, R, 2>::NP, BatchShape<Q, R, 2>::MB, BatchShape<Q, R, 2>::SPLIT>(b);
     }
 }
 
@@ -308,9 +310,9 @@ template <int Q, typename S, typename R> int Impl<Q, S, R>::batch_launch(lbm_bat
         if (int rc = cuda_error(cudaMemsetAsync((char*)b->d_sched + sizeof(int), 0, clear, b->stream), "batch clear"))
             return rc;
         switch (b->variant) {
-            case 0: launch_shape<BatchShape<Q, R, 0>::TX, BatchShape<Q, R, 0>::TY, BatchShape<Q, R, 0>::NP, BatchShape<Q, R, 0>::MB>(b); break;
-            case 1: launch_shape<BatchShape<Q, R, 1>::TX, BatchShape<Q, R, 1>::TY, BatchShape<Q, R, 1>::NP, BatchShape<Q, R, 1>::MB>(b); break;
-            default: launch_shape<BatchShape<Q, R, 2>::TX, BatchShape<Q, R, 2>::TY, BatchShape<Q, R, 2>::NP, BatchShape<Q, R, 2>::MB>(b); break;
+            case 0: launch_shape<BatchShape<Q, R, 0>::TX, BatchShape<Q, R, 0>::TY, BatchShape<Q, R, 0>::NP, BatchShape<Q, R, 0>::MB, BatchShape<Q, R, 0>::SPLIT>(b); break;
+            case 1: launch_shape<BatchShape<Q, R, 1>::TX, BatchShape<Q, R, 1>::TY, BatchShape<Q, R, 1>::NP, BatchShape<Q, R, 1>::MB, BatchShape<Q, R, 1>::SPLIT>(b); break;
+            default: launch_shape<BatchShape<Q, R, 2>::TX, BatchShape<Q, R, 2>::TY, BatchShape<Q, R, 2>::NP, BatchShape<Q, R, 2>::MB, BatchShape<Q, R, 2>::SPLIT>(b); break;
         }
     }
     if (advance && !b->doms.empty()) {

@@ -229,9 +229,13 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
     }
     // the moments of tile node (ta, tb) of plane m
     __device__ void m_interior(int m, int ta, int tb) const {
-        m_node(wrapi(m, G.nm) * plane_n, slotn(m, Sh::kPhiSlots), slotn(m, Sh::kRutSlots), (tb + RB) * RW + ta + 2);
+        m_node<true>(wrapi(m, G.nm) * plane_n, slotn(m, Sh::kPhiSlots), slotn(m, Sh::kRutSlots),
+                     (tb + RB) * RW + ta + 2);
     }
-    // Phi of ring node r, and rho, u, T if r lies in the 1-ring region
+    // Phi of ring node r, and rho, u, T if r lies in the 1-ring region.
+    // KEEP: the node is the caller's own, reloaded by its C stage three
+    // planes later, so its lines get the L2 evict-last hint.
+    template <bool KEEP = false>
     __device__ __forceinline__ void m_node(int plane_off, int sp, int sr, int r) const {
         const R third = R(1.0 / 3.0);
         {
@@ -240,7 +244,11 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
             R fN[Q], fG[Q];
 #pragma unroll
             for (int k = 0; k < Q; ++k)
-                ld2(src, pair_index(k, nn, n), R(V::w(k)) * p->rho_ref, R(V::w(k)) * p->E_ref, fN[k], fG[k]);
+                if (KEEP && !COH)
+                    Store<S, R>::load2_keep(src, pair_index(k, nn, n), R(V::w(k)) * p->rho_ref,
+                                            R(V::w(k)) * p->E_ref, fN[k], fG[k]);
+                else
+                    ld2(src, pair_index(k, nn, n), R(V::w(k)) * p->rho_ref, R(V::w(k)) * p->E_ref, fN[k], fG[k]);
             R rho = 0, ja = 0, jb = 0, jm = 0, E = 0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
@@ -654,8 +662,8 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 
 // FAULT: the item fault_item of step 0 does not report its completion
 // (tests of the bounded waits only).  XW: some domain has walls on the
-// tile-plane axes.
-template <int Q, typename S, typename R, int TX, int TY, int NP, int MB, bool FAULT, bool XW>
+// tile-plane axes.  SPLIT: the consumers form their own nodes' moments.
+template <int Q, typename S, typename R, int TX, int TY, int NP, int MB, bool FAULT, bool XW, bool SPLIT>
 __global__ void __launch_bounds__(TX* TY + NP, MB) fused_batch_kernel(const BatchItem* __restrict__ items,
                                                                   const DomainDesc<R>* __restrict__ doms,
                                                                   int n_items, BatchSched* sched, int n_doms,
@@ -704,7 +712,7 @@ __global__ void __launch_bounds__(TX* TY + NP, MB) fused_batch_kernel(const Batc
         if (active && go_sh) {
             const int in = (d->cur + s) & 1;
             const MarchGeom G = d->G;
-            fused_tile<Q, S, R, TX, TY, NP, false, true, XW>((const S*)d->pop[in], (S*)d->pop[in ^ 1], &kp, G,
+            fused_tile<Q, S, R, TX, TY, NP, false, true, XW, SPLIT>((const S*)d->pop[in], (S*)d->pop[in ^ 1], &kp, G,
                                                          kp.step + (unsigned)s, it.a0, it.b0, it.zb, d->cnt,
                                                          smem_raw);
         }

@@ -105,36 +105,26 @@ __host__ __device__ __forceinline__ size_t pair_index(int k, long long nn, long 
 }
 
 template <typename S, typename R> struct Store;
-// load_last: the same load for the last use of a value on this SM (the fused
-// step's consumer reload); L1::no_allocate leaves L1 to the lines the moment
-// stage will still reuse.  load2 / store2: the pair (N_k, g_k) at pair index
-// i (shifts sN, sG; random bits rN, rG of the FP16 rounding), one access.
+// load: one value at element index i (the set-major checkpoint layout).
+// load2 / store2: the pair (N_k, g_k) at pair index i in one access (shifts
+// sN, sG; random bits rN, rG of the FP16 rounding).  load2_keep: a first read
+// of lines the same SM reads again soon (L2 evict-last where it pays).
+// load2_last: the read of a value's last use on this SM (the fused step's
+// consumer reload); L1::no_allocate leaves L1 to the lines the moment stage
+// will still reuse.  The _coh forms skip the non-coherent path, for data
+// other CTAs of the same launch wrote (read after an acquire of their
+// release).
 
 template <> struct Store<double, double> {
     static constexpr bool kStochastic = false;
     __device__ static double load(const double* p, size_t i, double) { return p[i]; }
-    __device__ static double load_last(const double* p, size_t i, double) {
-        double v;
-        asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p + i));
-        return v;
-    }
-    __device__ static void store(double* p, size_t i, double v, double, unsigned = 0) { p[i] = v; }
-    // the same loads without the non-coherent path, for data other CTAs of
-    // the same launch wrote (read after an acquire of their release)
-    __device__ static double load_coh(const double* p, size_t i, double) {
-        double v;
-        asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p + i) : "memory");
-        return v;
-    }
-    __device__ static double load_last_coh(const double* p, size_t i, double) {
-        double v;
-        asm volatile("ld.global.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p + i) : "memory");
-        return v;
-    }
     __device__ static void load2(const double* p, size_t i, double, double, double& a, double& b) {
         const double2 v = __ldg(reinterpret_cast<const double2*>(p) + i);
         a = v.x;
         b = v.y;
+    }
+    __device__ static void load2_keep(const double* p, size_t i, double sN, double sG, double& a, double& b) {
+        load2(p, i, sN, sG, a, b);
     }
     __device__ static void load2_last(const double* p, size_t i, double, double, double& a, double& b) {
         asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p + 2 * i));
@@ -155,26 +145,15 @@ template <> struct Store<double, double> {
 template <> struct Store<float, float> {
     static constexpr bool kStochastic = false;
     __device__ static float load(const float* p, size_t i, float) { return __ldg(p + i); }
-    __device__ static float load_last(const float* p, size_t i, float) {
-        float v;
-        asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p + i));
-        return v;
-    }
-    __device__ static void store(float* p, size_t i, float v, float, unsigned = 0) { p[i] = v; }
-    __device__ static float load_coh(const float* p, size_t i, float) {
-        float v;
-        asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p + i) : "memory");
-        return v;
-    }
-    __device__ static float load_last_coh(const float* p, size_t i, float) {
-        float v;
-        asm volatile("ld.global.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p + i) : "memory");
-        return v;
-    }
     __device__ static void load2(const float* p, size_t i, float, float, float& a, float& b) {
         const float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
         a = v.x;
         b = v.y;
+    }
+    __device__ static void load2_keep(const float* p, size_t i, float, float, float& a, float& b) {
+        unsigned long long pol;
+        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+        asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(a), "=f"(b) : "l"(p + 2 * i), "l"(pol));
     }
     __device__ static void load2_last(const float* p, size_t i, float, float, float& a, float& b) {
         asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "l"(p + 2 * i));
@@ -191,44 +170,25 @@ template <> struct Store<float, float> {
     }
 };
 
+// FP16 shifted storage: a pair is one 32-bit word, N_k in the low half, g_k in
+// the high half.  rnd13: 13 random bits; adding them below the 10 FP16
+// mantissa bits of the FP32 value and rounding toward zero rounds the
+// magnitude up with probability equal to the discarded fraction (unbiased
+// for FP16-normal values).  The conversion drops the 13 low bits itself.
 template <> struct Store<__half, float> {
     static constexpr bool kStochastic = true;
     __device__ static float load(const __half* p, size_t i, float shift) {
         return __half2float(__ldg(p + i)) + shift;
     }
-    __device__ static float load_last(const __half* p, size_t i, float shift) {
-        unsigned short b;
-        asm("ld.global.nc.L1::no_allocate.b16 %0, [%1];" : "=h"(b) : "l"(p + i));
-        return __half2float(__ushort_as_half(b)) + shift;
-    }
-    __device__ static float load_coh(const __half* p, size_t i, float shift) {
-        unsigned short b;
-        asm volatile("ld.global.b16 %0, [%1];" : "=h"(b) : "l"(p + i) : "memory");
-        return __half2float(__ushort_as_half(b)) + shift;
-    }
-    __device__ static float load_last_coh(const __half* p, size_t i, float shift) {
-        unsigned short b;
-        asm volatile("ld.global.L1::no_allocate.b16 %0, [%1];" : "=h"(b) : "l"(p + i) : "memory");
-        return __half2float(__ushort_as_half(b)) + shift;
-    }
-    // rnd13: 13 random bits; adding them below the 10 FP16 mantissa bits of
-    // the FP32 value and truncating rounds the magnitude up with probability
-    // equal to the discarded fraction (unbiased for FP16-normal values)
-    __device__ static unsigned short round(float v, float shift, unsigned rnd13) {
-        unsigned b = __float_as_uint(v - shift);
-        b = (b + (rnd13 & 0x1FFFu)) & ~0x1FFFu;
-        return __half_as_ushort(__float2half_rz(__uint_as_float(b)));
-    }
-    __device__ static void store(__half* p, size_t i, float v, float shift, unsigned rnd13 = 0) {
-        p[i] = __ushort_as_half(round(v, shift, rnd13));
-    }
-    // a pair is one 32-bit word: N_k in the low half, g_k in the high half
     __device__ static void unpack(unsigned w, float sN, float sG, float& a, float& b) {
         a = __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))) + sN;
         b = __half2float(__ushort_as_half((unsigned short)(w >> 16))) + sG;
     }
     __device__ static void load2(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
         unpack(__ldg(reinterpret_cast<const unsigned*>(p) + i), sN, sG, a, b);
+    }
+    __device__ static void load2_keep(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
+        load2(p, i, sN, sG, a, b);
     }
     __device__ static void load2_last(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
         unsigned w;
@@ -245,9 +205,14 @@ template <> struct Store<__half, float> {
         asm volatile("ld.global.L1::no_allocate.b32 %0, [%1];" : "=r"(w) : "l"(p + 2 * i) : "memory");
         unpack(w, sN, sG, a, b);
     }
+    // both halves rounded toward zero by one packed conversion (g_k high)
     __device__ static void store2(__half* p, size_t i, float a, float b, float sN, float sG, unsigned rN = 0,
                                   unsigned rG = 0) {
-        reinterpret_cast<unsigned*>(p)[i] = (unsigned)round(a, sN, rN) | ((unsigned)round(b, sG, rG) << 16);
+        const float ra = __uint_as_float(__float_as_uint(a - sN) + (rN & 0x1FFFu));
+        const float rb = __uint_as_float(__float_as_uint(b - sG) + (rG & 0x1FFFu));
+        unsigned w;
+        asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(rb), "f"(ra));
+        reinterpret_cast<unsigned*>(p)[i] = w;
     }
 };
 

@@ -261,7 +261,7 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
 #pragma unroll
             for (int k = 0; k < Q; ++k) E += fG[k];
             const R T = E / (rho * p->c_v);
-            const R U = eos_pressure(*p, rho, T) - rho * third;
+            const R U = fma(-rho, third, eos_pressure(*p, rho, T));
             phi(sp, r) = U < R(0) ? sqrt(-U) : R(0);
             const int fa = ra - 1, fb = rb - (RB - FB);
             if (fa >= 0 && fa < FW && fb >= 0 && fb < Sh::FH) {
@@ -295,21 +295,24 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
                 const int s_m = M::m(k) == 0 ? sp0 : (M::m(k) > 0 ? spm : spp);
                 const R pp = phi(s_p, (rb + M::b(k)) * RW + ra + M::a(k));
                 const R pm = phi(s_m, (rb - M::b(k)) * RW + ra - M::a(k));
-                const R d = pp - pm;
-                const R d2 = d * (pp + pm);
+                const R d = pp - pm, sum = pp + pm;
                 const bool nearest = M::a(k) * M::a(k) + M::b(k) * M::b(k) + M::m(k) * M::m(k) == 1;
                 R* s1 = nearest ? n1 : q1;
                 R* s2 = nearest ? n2 : q2;
-                if (M::a(k) == 1) { s1[0] += d2; s2[0] += d; } else if (M::a(k) == -1) { s1[0] -= d2; s2[0] -= d; }
-                if (M::b(k) == 1) { s1[1] += d2; s2[1] += d; } else if (M::b(k) == -1) { s1[1] -= d2; s2[1] -= d; }
-                if (M::m(k) == 1) { s1[2] += d2; s2[2] += d; } else if (M::m(k) == -1) { s1[2] -= d2; s2[2] -= d; }
+                // s1 += +-d (Phi+ + Phi-) as one fused multiply-add per axis
+                if (M::a(k) == 1) { s1[0] = fma(d, sum, s1[0]); s2[0] += d; }
+                else if (M::a(k) == -1) { s1[0] = fma(-d, sum, s1[0]); s2[0] -= d; }
+                if (M::b(k) == 1) { s1[1] = fma(d, sum, s1[1]); s2[1] += d; }
+                else if (M::b(k) == -1) { s1[1] = fma(-d, sum, s1[1]); s2[1] -= d; }
+                if (M::m(k) == 1) { s1[2] = fma(d, sum, s1[2]); s2[2] += d; }
+                else if (M::m(k) == -1) { s1[2] = fma(-d, sum, s1[2]); s2[2] -= d; }
             }
             const R rho = rut(sr, 0, r), ph0 = phi(sp0, rb * RW + ra);
-            const R scale = inv_alpha / rho;
+            const R scale = inv_alpha / rho, Bph0 = B * ph0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const R s1 = n1[a] + G2 * q1[a], s2 = n2[a] + G2 * q2[a];
-                du(sd, a, r) = (A * s1 + B * ph0 * s2) * scale + gv[a];
+                const R s1 = fma(G2, q1[a], n1[a]), s2 = fma(G2, q2[a], n2[a]);
+                du(sd, a, r) = fma(fma(A, s1, Bph0 * s2), scale, gv[a]);
             }
         }
     }
@@ -348,7 +351,7 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
 
         // finite-difference dE along a, b and the march axis (Sec. 4, Sec. 6.2)
         R div = 0, cond = 0;
-        const R lc = conductivity(*p, rho);
+        const R lc = conductivity(*p, rho), half_lc = lc * R(0.5);
         // one axis of the differences; g: bit 0 / 1 the low / high neighbour is
         // the ghost beyond a wall, whose values are then own_u (normal
         // velocity), T_lo / T_hi and the node's own density
@@ -358,30 +361,31 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
                 if (g & 2) { uu = own_u; Tu = T_hi; ru = rho; }
                 if (g & 1) { ud = own_u; Td = T_lo; rd = rho; }
             }
-            div += (uu - ud) / R(2);
-            const R lu = (lc + conductivity(*p, ru)) / R(2);
-            const R ld = (lc + conductivity(*p, rd)) / R(2);
-            cond += lu * (Tu - T) - ld * (T - Td);
+            div = fma(uu - ud, R(0.5), div);
+            // face conductivities, the mean of the two nodes'
+            const R lu = fma(conductivity(*p, ru), R(0.5), half_lc);
+            const R ld = fma(conductivity(*p, rd), R(0.5), half_lc);
+            cond = fma(-ld, T - Td, fma(lu, Tu - T, cond));
         };
         // axes across the tile: neighbouring ring nodes, or (only for nodes
         // beside a wall) the node itself mirrored across it: normal velocity
         // negated, T mirrored or reflected about the wall temperature
-        axis(rut(sr, 1, fc + 1) + du(sd, 0, fc + 1) / R(2), rut(sr, 1, fc - 1) + du(sd, 0, fc - 1) / R(2),
+        axis(fma(du(sd, 0, fc + 1), R(0.5), rut(sr, 1, fc + 1)), fma(du(sd, 0, fc - 1), R(0.5), rut(sr, 1, fc - 1)),
              rut(sr, 4, fc + 1), rut(sr, 4, fc - 1), rut(sr, 0, fc + 1), rut(sr, 0, fc - 1), edge & 3,
-             -(u[0] + dv[0] / R(2)), p->T_fixed_x[0] ? R(2) * p->T_x[0] - T : T,
+             -fma(dv[0], R(0.5), u[0]), p->T_fixed_x[0] ? R(2) * p->T_x[0] - T : T,
              p->T_fixed_x[1] ? R(2) * p->T_x[1] - T : T);
         if (Q == 19)
-            axis(rut(sr, 2, fc + FW) + du(sd, 1, fc + FW) / R(2), rut(sr, 2, fc - FW) + du(sd, 1, fc - FW) / R(2),
+            axis(fma(du(sd, 1, fc + FW), R(0.5), rut(sr, 2, fc + FW)), fma(du(sd, 1, fc - FW), R(0.5), rut(sr, 2, fc - FW)),
                  rut(sr, 4, fc + FW), rut(sr, 4, fc - FW), rut(sr, 0, fc + FW), rut(sr, 0, fc - FW), (edge >> 2) & 3,
-                 -(u[1] + dv[1] / R(2)), p->T_fixed_y[0] ? R(2) * p->T_y[0] - T : T,
+                 -fma(dv[1], R(0.5), u[1]), p->T_fixed_y[0] ? R(2) * p->T_y[0] - T : T,
                  p->T_fixed_y[1] ? R(2) * p->T_y[1] - T : T);
         {   // march axis: neighbouring planes, or the node itself mirrored across a wall
             const bool gu = walls && c + 1 >= nm, gd = walls && c - 1 < 0;
             const int su = slotn(c + 1, Sh::kRutSlots), sdn = slotn(c - 1, Sh::kRutSlots);
             const int du_u = slotn(c + 1, Sh::kDuSlots), du_d = slotn(c - 1, Sh::kDuSlots);
-            const R own = -(u[2] + dv[2] / R(2));
-            const R uu = gu ? own : rut(su, 3, fc) + du(du_u, 2, fc) / R(2);
-            const R ud = gd ? own : rut(sdn, 3, fc) + du(du_d, 2, fc) / R(2);
+            const R own = -fma(dv[2], R(0.5), u[2]);
+            const R uu = gu ? own : fma(du(du_u, 2, fc), R(0.5), rut(su, 3, fc));
+            const R ud = gd ? own : fma(du(du_d, 2, fc), R(0.5), rut(sdn, 3, fc));
             const R Tu = gu ? (p->T_fixed_hi ? R(2) * p->T_hi - T : T) : rut(su, 4, fc);
             const R Td = gd ? (p->T_fixed_lo ? R(2) * p->T_lo - T : T) : rut(sdn, 4, fc);
             const R ru = gu ? rho : rut(su, 0, fc);
@@ -393,7 +397,7 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
         if (p->pressure_work) dE += -P * div;
         if (p->conduction) dE += cond;
         if (p->latent != R(0)) dE += latent_heat(*p, rho, T, div);
-        if (P - rho * third >= R(0)) atomicAdd(&cnt->clamps, 1ull);
+        if (fma(-rho, third, P) >= R(0)) atomicAdd(&cnt->clamps, 1ull);
 
         R E = 0;
 #pragma unroll
@@ -426,9 +430,10 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
         // (WALL: some directions bounce back) and once for all other planes
         auto collide = [&](auto wall_tag) {
             constexpr bool WALL = decltype(wall_tag)::value;
-            auto emit = [&](int k, R e0, R de, R fv, R hvk) {
-                const R fo = fma(fv, fN, fma(rho_om, e0, rho * de));
-                const R ho = fma(hvk, fG, fma(E_omE, e0, E_pf * de));
+            // a: rho (omega e0 + de), b: E (omega_E e0 + [pseudoforce] de) of direction k
+            auto emit = [&](int k, R a, R b, R fv, R hvk) {
+                const R fo = fma(fv, fN, a);
+                const R ho = fma(hvk, fG, b);
                 // push to x + c_k, or bounce back at a wall on the march axis
                 const bool bounce = WALL && ((M::m(k) == -1 && wall_lo) || (M::m(k) == 1 && wall_hi) ||
                                              (M::a(k) == -1 && edge_a_lo) || (M::a(k) == 1 && edge_a_hi) ||
@@ -446,7 +451,8 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
             };
             {
                 const R w0 = R(V::w(0));
-                emit(0, w0 * base0, w0 * dbase, fv[0], hv[0]);
+                const R e0 = w0 * base0, de = w0 * dbase;
+                emit(0, fma(rho_om, e0, rho * de), fma(E_omE, e0, E_pf * de), fv[0], hv[0]);
             }
 #pragma unroll
             for (int k = 1; k < Q; k += 2) {
@@ -457,8 +463,13 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
                 if (M::m(k) == 1) { cu += u[2]; cd += dv[2]; } else if (M::m(k) == -1) { cu -= u[2]; cd -= dv[2]; }
                 const R ev = wk * fma(R(4.5) * cu, cu, base0), od = (R(3) * wk) * cu;
                 const R dv_e = wk * fma(R(4.5) * cd, fma(R(2), cu, cd), dbase), dv_o = (R(3) * wk) * cd;
-                emit(k, ev + od, dv_e + dv_o, fv[k], hv[k]);
-                emit(k + 1, ev - od, dv_e - dv_o, fv[k + 1], hv[k + 1]);
+                // direction k takes e0 = ev + od, de = dv_e + dv_o and k + 1
+                // the differences: the even and odd parts of the sources are
+                // formed once for both
+                const R aE = fma(rho_om, ev, rho * dv_e), aO = fma(rho_om, od, rho * dv_o);
+                const R bE = fma(E_omE, ev, E_pf * dv_e), bO = fma(E_omE, od, E_pf * dv_o);
+                emit(k, aE + aO, bE + bO, fv[k], hv[k]);
+                emit(k + 1, aE - aO, bE - bO, fv[k + 1], hv[k + 1]);
             }
         };
         if (wall_lo || wall_hi || edge) collide(std::true_type{});

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) fields_kernel(const S* __restrict__ pop, 
     R rho, jx, jy, jz, E;
     node_moments<Q, S, R>(pop, nn, i, p, rho, jx, jy, jz, E);
     R T = E / (rho * p.c_v);
-    R U = eos_pressure(p, rho, T) - rho * R(1.0 / 3.0);
+    R U = fma(-rho, R(1.0 / 3.0), eos_pressure(p, rho, T));
     R Phi;
     if (U < R(0)) {
         Phi = sqrt(-U);
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(256) init_kernel(S* __restrict__ pop, const do
     const R E = rho * eps;
     const R T = eps / p.c_v;
     bool ok = finite_pos(rho) && finite_pos(eps) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
-    if (ok) ok = eos_pressure(p, rho, T) - rho * R(1.0 / 3.0) < R(0);
+    if (ok) ok = fma(-rho, R(1.0 / 3.0), eos_pressure(p, rho, T)) < R(0);
     if (!ok) atomicAdd(&cnt->bad, 1ull);
     // stability pre-flight: (dp/drho)_T <= (h/dt)^2 + theta (Sec. 3) and the
     // explicit conduction limit chi dt/h^2 < 0.5/d (Sec. 6.1)

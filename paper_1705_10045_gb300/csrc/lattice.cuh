@@ -165,8 +165,14 @@ template <> struct Store<float, float> {
         asm volatile("ld.global.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "l"(p + 2 * i)
                      : "memory");
     }
+    // the stored pair is read again only in the next step, after the whole
+    // domain has streamed through L2: evict-first keeps L2 for the lines the
+    // step itself still reads
     __device__ static void store2(float* p, size_t i, float a, float b, float, float, unsigned = 0, unsigned = 0) {
-        reinterpret_cast<float2*>(p)[i] = make_float2(a, b);
+        unsigned long long pol;
+        asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+        asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p + 2 * i), "f"(a), "f"(b), "l"(pol)
+                     : "memory");
     }
 };
 
@@ -246,7 +252,7 @@ template <typename R> struct KParams {
 template <typename R>
 __device__ __forceinline__ R eos_pressure(const KParams<R>& p, R rho, R T) {
     R Te = p.barotropic ? p.T0 : T;
-    return p.kappa * (R(8) * rho * Te / (R(3) - rho) - R(3) * rho * rho);
+    return p.kappa * fma(R(-3) * rho, rho, R(8) * rho * Te / (R(3) - rho));
 }
 
 template <typename R>

@@ -438,7 +438,7 @@ def batched_bench(count: int = 256, steps: int = BATCH_STEPS):
     }
 
 
-def serving_bench(count: int = 24, storage: int = None, seed: int = 5, rate: float = 200.0):
+def serving_bench(count: int = 128, storage: int = None, seed: int = 5, rate: float = 200.0):
     """Serving stream: Poisson arrivals at 200 jobs/s of D3Q19 droplet/slab
     cubes, sides uniform in [32, 192], steps uniform in [500, 5000], T in
     [0.7, 0.9], constant thermal diffusivity 0.05, FP32 storage (FP16 when
@@ -565,7 +565,8 @@ def main():
     ap.add_argument("--no-slabs", action="store_true", help="skip the slab-decomposition measurement")
     ap.add_argument("--no-d2q9", action="store_true", help="skip the single-domain D2Q9 measurement")
     ap.add_argument("--d2q9-size", default=None, help="NXxNY of a smaller D2Q9 domain (profiling)")
-    ap.add_argument("--serve-jobs", type=int, default=24)
+    ap.add_argument("--serve-jobs", type=int, default=128,
+                    help="arrivals served in each serving measurement (saturated and below saturation)")
     ap.add_argument("--size", default=None, help="NXxNYxNZ of a smaller pool-boiling box (profiling)")
     ap.add_argument("--mode", default="slabs", choices=["slabs", "replicas"],
                     help="with several ranks: one domain in z-slabs (default) or a replica per rank")
@@ -709,7 +710,7 @@ def main():
             # the 200 jobs/s stream saturates the GPU; latency percentiles of a
             # stream below saturation: arrivals at 0.7x the served completion rate
             sub_rate = 0.7 * line["serving"]["value"]
-            line["serving_below_saturation"] = serving_bench(12, seed=6, rate=sub_rate)
+            line["serving_below_saturation"] = serving_bench(args.serve_jobs, seed=6, rate=sub_rate)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -192,14 +192,13 @@ template <int Q, typename S, typename R> struct Impl {
         G.na = h->p.nx;
         G.nb = Q == 9 ? 1 : h->p.ny;
         G.nm = Q == 9 ? h->p.ny : h->p.nz;
-        // planes per work item: enough items for about four waves of two CTAs
-        // per SM when the domain runs alone (a step of a domain ends only when
-        // its last item does), between 8 and 64 planes (longer items cost
-        // less ring recompute)
-        const long long tiles = (long long)((G.na + BTX - 1) / BTX) * ((G.nb + BTY - 1) / BTY);
-        long long c = (G.nm * tiles + 4 * 304 - 1) / (4 * 304);
-        c = c < 8 ? 8 : (c > 64 ? 64 : c);
-        G.chunk = (int)(c > G.nm ? G.nm : c);
+        // planes per work item: 64 (or the whole axis).  Every item recomputes
+        // the ring planes at its ends and, with the split moment stage, forms
+        // the moments of its first three planes in the producers alone, so long
+        // items pay; the items of the other domains of a batch fill the waves
+        // (measured: shorter items for four waves per domain gave 31 instead of
+        // 40 jobs/s on the D2Q9 batch and 2.1 instead of 2.4 served jobs/s)
+        G.chunk = G.nm < 64 ? G.nm : 64;
         return G;
     }
 
@@ -221,9 +220,12 @@ template <int Q, typename S, typename R> struct Impl {
                 const int tx = (dd.G.na + BTX - 1) / BTX, ty = (dd.G.nb + BTY - 1) / BTY;
                 const int tz = (dd.G.nm + dd.G.chunk - 1) / dd.G.chunk;
                 dd.n_items = tx * ty * tz;
-                for (int z = 0; z < tz; ++z)
-                    for (int y = 0; y < ty; ++y)
-                        for (int x = 0; x < tx; ++x) items.push_back({(int)d, x * BTX, y * BTY, z * dd.G.chunk});
+                // only the domains that step in this request get work items: a
+                // paused domain would cost every persistent CTA a pass over them
+                if (d < b->in_table.size() && b->in_table[d])
+                    for (int z = 0; z < tz; ++z)
+                        for (int y = 0; y < ty; ++y)
+                            for (int x = 0; x < tx; ++x) items.push_back({(int)d, x * BTX, y * BTY, z * dd.G.chunk});
             }
             descs[d] = dd;
         }

@@ -45,6 +45,8 @@ struct lbm_batch {
     void* h_descs = nullptr;            // pinned staging of the descriptors
     size_t descs_cap = 0;
     bool dirty = true;                  // work table out of date
+    std::vector<char> in_table;         // slot -> its tiles are in the work table (a step budget
+                                        // this request; every domain while tuning)
     int variant = 0;                    // CTA shape (see lbm_batch_variants)
     void* d_sched = nullptr;            // lbm::BatchSched + done[descs_cap] + aborted[descs_cap]
     int* h_steps = nullptr;             // pinned staging of the request's step count

@@ -95,12 +95,21 @@ int ensure_descs(lbm_batch* b) {
     return LBM_OK;
 }
 
-// Work table for the current slots and shape; descriptors restaged.
-int rebuild(lbm_batch* b) {
+// Domains whose tiles belong in the work table: those with a step budget
+// (all: every domain, for the tuner's one step of each).
+std::vector<char> table_set(const lbm_batch* b, bool all) {
+    std::vector<char> in(b->doms.size(), 0);
+    for (size_t d = 0; d < b->doms.size(); ++d) in[d] = b->doms[d] && (all || b->budget[d] > 0);
+    return in;
+}
+
+// Work table for the current slots, budgets and shape; descriptors restaged.
+int rebuild(lbm_batch* b, bool all = false) {
     if (int rc = cudaStreamSynchronize(b->stream)) return cuda_error((cudaError_t)rc, "batch synchronize");
     if (int rc = ensure_descs(b)) return rc;
+    b->in_table = table_set(b, all);
     if (int rc = be_build(b)) return rc;
-    b->dirty = false;
+    b->dirty = all;   // a table of every domain serves the tuner only
     return LBM_OK;
 }
 
@@ -266,7 +275,7 @@ int lbm_batch_step(lbm_batch* b, int n) {
     }
     if (n == 0) return LBM_OK;
     cudaSetDevice(b->common.device);
-    if (b->dirty)
+    if (b->dirty || table_set(b, false) != b->in_table)
         if (int rc = rebuild(b)) return rc;
     // the pinned staging may still feed the previous request's copy
     if (int rc = cuda_error(cudaStreamSynchronize(b->stream), "batch synchronize")) return rc;
@@ -384,7 +393,7 @@ int lbm_batch_tune(lbm_batch* b, int reps, int* best, double* ms) {
     int rc = LBM_OK;
     for (int v = 0; v < nv && !rc; ++v) {
         b->variant = v;
-        if ((rc = rebuild(b))) break;
+        if ((rc = rebuild(b, true))) break;
         std::vector<long long> keep = b->budget;
         for (auto& x : b->budget) x = 1;
         if ((rc = upload_descs(b, 1))) break;

@@ -195,14 +195,28 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
     int plane_n;
     unsigned step;   // step counter of this launch (seeds FP16 stochastic rounding)
 
-    // the pair (N_k, g_k) at pair index i of q
+    // the pair (N_k, g_k) at pair index i of q.  With shifted storage (FP16)
+    // the stages work on the stored values N_k - w_k rho_ref, g_k - w_k E_ref
+    // themselves: the moments add rho_ref and E_ref once, and the collision
+    // writes shifted values (see c_stage), so no value is shifted on its own.
+    static constexpr bool kSh = Store<S, R>::kShifted;
     __device__ static void ld2(const S* q, size_t i, R sN, R sG, R& a, R& b) {
-        if (COH) Store<S, R>::load2_coh(q, i, sN, sG, a, b);
-        else Store<S, R>::load2(q, i, sN, sG, a, b);
+        if constexpr (kSh) {
+            if (COH) Store<S, R>::load2_coh_raw(q, i, a, b);
+            else Store<S, R>::load2_raw(q, i, a, b);
+        } else {
+            if (COH) Store<S, R>::load2_coh(q, i, sN, sG, a, b);
+            else Store<S, R>::load2(q, i, sN, sG, a, b);
+        }
     }
     __device__ static void ld2_last(const S* q, size_t i, R sN, R sG, R& a, R& b) {
-        if (COH) Store<S, R>::load2_last_coh(q, i, sN, sG, a, b);
-        else Store<S, R>::load2_last(q, i, sN, sG, a, b);
+        if constexpr (kSh) {
+            if (COH) Store<S, R>::load2_last_coh_raw(q, i, a, b);
+            else Store<S, R>::load2_last_raw(q, i, a, b);
+        } else {
+            if (COH) Store<S, R>::load2_last_coh(q, i, sN, sG, a, b);
+            else Store<S, R>::load2_last(q, i, sN, sG, a, b);
+        }
     }
     __device__ R& phi(int slot, int r) const { return phis[slot * R_ + r]; }
     __device__ R& rut(int slot, int f, int r) const { return ruts[(slot * Sh::kRut + f) * F_ + r]; }
@@ -244,7 +258,7 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
             R fN[Q], fG[Q];
 #pragma unroll
             for (int k = 0; k < Q; ++k)
-                if (KEEP && !COH)
+                if (KEEP && !COH && !kSh)
                     Store<S, R>::load2_keep(src, pair_index(k, nn, n), R(V::w(k)) * p->rho_ref,
                                             R(V::w(k)) * p->E_ref, fN[k], fG[k]);
                 else
@@ -260,6 +274,10 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
             }
 #pragma unroll
             for (int k = 0; k < Q; ++k) E += fG[k];
+            if constexpr (kSh) {   // sums of shifted values: sum_k w_k = 1, sum_k w_k c_k = 0
+                rho += p->rho_ref;
+                E += p->E_ref;
+            }
             const R T = E / (rho * p->c_v);
             const R U = fma(-rho, third, eos_pressure(*p, rho, T));
             phi(sp, r) = U < R(0) ? sqrt(-U) : R(0);
@@ -402,6 +420,7 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
         R E = 0;
 #pragma unroll
         for (int k = 0; k < Q; ++k) E += hv[k];
+        if constexpr (kSh) E += p->E_ref;
         if (!(finite_pos(rho) && finite_pos(E))) atomicAdd(&cnt->bad, 1ull);
         const R dEoverE = dE / E;
         // node offsets of x + c_k: +-1 along a and b (periodic), along the
@@ -424,6 +443,11 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
         const R om = p->omega, omE = p->omega_E;
         const R fN = R(1) - om, fG = R(1) - omE + dEoverE;
         const R rho_om = rho * om, E_omE = E * omE, E_pf = p->pseudoforce ? E : R(0);
+        // shifted storage: with N_k = N'_k + w_k rho_ref and g_k = g'_k + w_k E_ref
+        //   N*'_k = (1 - omega) N'_k + rho (omega e0_k + de_k) - omega w_k rho_ref
+        //   g*'_k = fG g'_k + E (omega_E e0_k + [pf] de_k) + (fG - 1) w_k E_ref
+        // so the shifts enter as w_k nsh and w_k gsh in the source terms
+        const R nsh = kSh ? -om * p->rho_ref : R(0), gsh = kSh ? (fG - R(1)) * p->E_ref : R(0);
         const unsigned nbits = Store<S, R>::kStochastic ? node_bits(step, (unsigned)n) : 0u;
         S* dk = dst + 2 * (size_t)n;        // pair k of the node's slot (walks over k)
         // the collision and push, instantiated once for planes next to a wall
@@ -444,15 +468,21 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
                 if (M::m(k) == 1) to += dM_p; else if (M::m(k) == -1) to += dM_m;
                 // opposite directions share a weight, so the FP16 shift of slot ko is w_k ref
                 const R wk = R(V::w(k));
-                const unsigned rN = slot_bits(nbits, k), rG = slot_bits(nbits, Q + k);
+                unsigned rN = 0, rG = 0;
+                if (Store<S, R>::kStochastic) pair_bits(nbits, k, rN, rG);
                 const long long off = bounce ? (long long)(opposite(k) - k) * (long long)nn : (long long)to;
-                Store<S, R>::store2(dk + 2 * off, 0, fo, ho, wk * p->rho_ref, wk * p->E_ref, rN, rG);
+                if constexpr (kSh) Store<S, R>::store2_raw(dk + 2 * off, 0, fo, ho, rN, rG);
+                else Store<S, R>::store2(dk + 2 * off, 0, fo, ho, wk * p->rho_ref, wk * p->E_ref, rN, rG);
                 dk += 2 * nn;
             };
             {
                 const R w0 = R(V::w(0));
                 const R e0 = w0 * base0, de = w0 * dbase;
-                emit(0, fma(rho_om, e0, rho * de), fma(E_omE, e0, E_pf * de), fv[0], hv[0]);
+                if constexpr (kSh)
+                    emit(0, fma(rho_om, e0, fma(rho, de, w0 * nsh)), fma(E_omE, e0, fma(E_pf, de, w0 * gsh)), fv[0],
+                         hv[0]);
+                else
+                    emit(0, fma(rho_om, e0, rho * de), fma(E_omE, e0, E_pf * de), fv[0], hv[0]);
             }
 #pragma unroll
             for (int k = 1; k < Q; k += 2) {
@@ -466,8 +496,9 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
                 // direction k takes e0 = ev + od, de = dv_e + dv_o and k + 1
                 // the differences: the even and odd parts of the sources are
                 // formed once for both
-                const R aE = fma(rho_om, ev, rho * dv_e), aO = fma(rho_om, od, rho * dv_o);
-                const R bE = fma(E_omE, ev, E_pf * dv_e), bO = fma(E_omE, od, E_pf * dv_o);
+                const R aE = kSh ? fma(rho_om, ev, fma(rho, dv_e, wk * nsh)) : fma(rho_om, ev, rho * dv_e);
+                const R bE = kSh ? fma(E_omE, ev, fma(E_pf, dv_e, wk * gsh)) : fma(E_omE, ev, E_pf * dv_e);
+                const R aO = fma(rho_om, od, rho * dv_o), bO = fma(E_omE, od, E_pf * dv_o);
                 emit(k, aE + aO, bE + bO, fv[k], hv[k]);
                 emit(k + 1, aE - aO, bE - bO, fv[k + 1], hv[k + 1]);
             }

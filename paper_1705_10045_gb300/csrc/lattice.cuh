@@ -82,13 +82,16 @@ __host__ __device__ __forceinline__ unsigned mix32(unsigned x) {
     return x;
 }
 
-// per-node random word of one step; the bits of slot s are the top bits of
-// node_bits * (2s + 1) * golden ratio constant
+// per-node random word of one step; the 13 bits of the pair of direction k
+// come from one product t = node_bits * (2k + 1) * golden ratio constant: its
+// top 13 bits for N_k and bits 6..18 for g_k
 __device__ __forceinline__ unsigned node_bits(unsigned step, unsigned n) {
     return mix32(n * 0x9E3779B1u ^ mix32(step + 0x632BE5ABu));
 }
-__device__ __forceinline__ unsigned slot_bits(unsigned nb, int slot) {
-    return (nb * ((2u * (unsigned)slot + 1u) * 0x9E3779B9u)) >> 19;
+__device__ __forceinline__ void pair_bits(unsigned nb, int k, unsigned& rN, unsigned& rG) {
+    const unsigned t = nb * ((2u * (unsigned)k + 1u) * 0x9E3779B9u);
+    rN = t >> 19;
+    rG = (t >> 6) & 0x1FFFu;
 }
 
 // Population layout in device memory.  Every kernel reads a node's N_k and
@@ -116,7 +119,7 @@ template <typename S, typename R> struct Store;
 // release).
 
 template <> struct Store<double, double> {
-    static constexpr bool kStochastic = false;
+    static constexpr bool kStochastic = false, kShifted = false;
     __device__ static double load(const double* p, size_t i, double) { return p[i]; }
     __device__ static void load2(const double* p, size_t i, double, double, double& a, double& b) {
         const double2 v = __ldg(reinterpret_cast<const double2*>(p) + i);
@@ -143,7 +146,7 @@ template <> struct Store<double, double> {
 };
 
 template <> struct Store<float, float> {
-    static constexpr bool kStochastic = false;
+    static constexpr bool kStochastic = false, kShifted = false;
     __device__ static float load(const float* p, size_t i, float) { return __ldg(p + i); }
     __device__ static void load2(const float* p, size_t i, float, float, float& a, float& b) {
         const float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
@@ -181,8 +184,10 @@ template <> struct Store<float, float> {
 // mantissa bits of the FP32 value and rounding toward zero rounds the
 // magnitude up with probability equal to the discarded fraction (unbiased
 // for FP16-normal values).  The conversion drops the 13 low bits itself.
+// The _raw forms move the stored, shifted values as they are (kShifted: a
+// kernel may do its arithmetic on shifted values and skip the shifts).
 template <> struct Store<__half, float> {
-    static constexpr bool kStochastic = true;
+    static constexpr bool kStochastic = true, kShifted = true;
     __device__ static float load(const __half* p, size_t i, float shift) {
         return __half2float(__ldg(p + i)) + shift;
     }
@@ -190,35 +195,63 @@ template <> struct Store<__half, float> {
         a = __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))) + sN;
         b = __half2float(__ushort_as_half((unsigned short)(w >> 16))) + sG;
     }
+    __device__ static void unpack_raw(unsigned w, float& a, float& b) {
+        a = __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu)));
+        b = __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+    }
+    __device__ static unsigned word(const __half* p, size_t i) { return __ldg(reinterpret_cast<const unsigned*>(p) + i); }
+    __device__ static unsigned word_last(const __half* p, size_t i) {
+        unsigned w;
+        asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(w) : "l"(p + 2 * i));
+        return w;
+    }
+    __device__ static unsigned word_coh(const __half* p, size_t i) {
+        unsigned w;
+        asm volatile("ld.global.b32 %0, [%1];" : "=r"(w) : "l"(p + 2 * i) : "memory");
+        return w;
+    }
+    __device__ static unsigned word_last_coh(const __half* p, size_t i) {
+        unsigned w;
+        asm volatile("ld.global.L1::no_allocate.b32 %0, [%1];" : "=r"(w) : "l"(p + 2 * i) : "memory");
+        return w;
+    }
     __device__ static void load2(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
-        unpack(__ldg(reinterpret_cast<const unsigned*>(p) + i), sN, sG, a, b);
+        unpack(word(p, i), sN, sG, a, b);
     }
     __device__ static void load2_keep(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
         load2(p, i, sN, sG, a, b);
     }
     __device__ static void load2_last(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
-        unsigned w;
-        asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(w) : "l"(p + 2 * i));
-        unpack(w, sN, sG, a, b);
+        unpack(word_last(p, i), sN, sG, a, b);
     }
     __device__ static void load2_coh(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
-        unsigned w;
-        asm volatile("ld.global.b32 %0, [%1];" : "=r"(w) : "l"(p + 2 * i) : "memory");
-        unpack(w, sN, sG, a, b);
+        unpack(word_coh(p, i), sN, sG, a, b);
     }
     __device__ static void load2_last_coh(const __half* p, size_t i, float sN, float sG, float& a, float& b) {
-        unsigned w;
-        asm volatile("ld.global.L1::no_allocate.b32 %0, [%1];" : "=r"(w) : "l"(p + 2 * i) : "memory");
-        unpack(w, sN, sG, a, b);
+        unpack(word_last_coh(p, i), sN, sG, a, b);
     }
-    // both halves rounded toward zero by one packed conversion (g_k high)
-    __device__ static void store2(__half* p, size_t i, float a, float b, float sN, float sG, unsigned rN = 0,
-                                  unsigned rG = 0) {
-        const float ra = __uint_as_float(__float_as_uint(a - sN) + (rN & 0x1FFFu));
-        const float rb = __uint_as_float(__float_as_uint(b - sG) + (rG & 0x1FFFu));
+    __device__ static void load2_raw(const __half* p, size_t i, float& a, float& b) { unpack_raw(word(p, i), a, b); }
+    __device__ static void load2_last_raw(const __half* p, size_t i, float& a, float& b) {
+        unpack_raw(word_last(p, i), a, b);
+    }
+    __device__ static void load2_coh_raw(const __half* p, size_t i, float& a, float& b) {
+        unpack_raw(word_coh(p, i), a, b);
+    }
+    __device__ static void load2_last_coh_raw(const __half* p, size_t i, float& a, float& b) {
+        unpack_raw(word_last_coh(p, i), a, b);
+    }
+    // both halves rounded toward zero by one packed conversion (g_k high);
+    // a, b already shifted
+    __device__ static void store2_raw(__half* p, size_t i, float a, float b, unsigned rN, unsigned rG) {
+        const float ra = __uint_as_float(__float_as_uint(a) + (rN & 0x1FFFu));
+        const float rb = __uint_as_float(__float_as_uint(b) + (rG & 0x1FFFu));
         unsigned w;
         asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(rb), "f"(ra));
         reinterpret_cast<unsigned*>(p)[i] = w;
+    }
+    __device__ static void store2(__half* p, size_t i, float a, float b, float sN, float sG, unsigned rN = 0,
+                                  unsigned rG = 0) {
+        store2_raw(p, i, a - sN, b - sG, rN, rG);
     }
 };
 

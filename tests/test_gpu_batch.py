@@ -53,6 +53,45 @@ def test_batch_d2q9_matches_jobs_run_alone(storage):
         batch.close()
 
 
+def test_batch_paused_domains_keep_their_state():
+    """A domain whose budget is 0 for a request (the serving loop's paused
+    jobs) takes no work items and keeps its state bit for bit; the stepping
+    domains are unaffected, and every domain, resumed, still matches the same
+    job run alone.  The work table changes with the set of stepping domains
+    (and the tuner's table of every domain is not kept for stepping)."""
+    jobs = [
+        (W.pool_boiling_3d(nx=40, ny=36, nz=24, depth=8, noise=1e-3, seed=3),
+         dict(nx=40, ny=36, nz=24, wall=1, T_fixed_lo=1, T_lo=0.95, gravity=(0.0, 0.0, -1e-5))),
+        (W.droplet_or_slab_3d(24, 0.8, "droplet", seed=7), dict(nx=24, ny=24, nz=24, chi_mode=1, chi=0.05)),
+        (W.droplet_or_slab_3d(19, 0.75, "slab", seed=8), dict(nx=19, ny=19, nz=19, chi_mode=1, chi=0.05)),
+    ]
+    batch = lbm.LbmBatch(lattice=19, storage=lbm.LBM_STORE_FP32)
+    try:
+        ids = [batch.add(f.rho, np.ascontiguousarray(f.u), 1.5 * f.T, 60, **kw) for f, kw in jobs]
+        batch.step(10)
+        frozen = batch.get_state(ids[1]).copy()
+        batch.set_budget(ids[1], 0)             # paused: 50 steps left, none this request
+        batch.step(20)
+        assert batch.status(ids[1]) == (10, 0)
+        assert np.array_equal(batch.get_state(ids[1]), frozen)
+        assert batch.status(ids[0]) == (30, 30) and batch.status(ids[2]) == (30, 30)
+        batch.set_budget(ids[1], 50)
+        batch.tune(reps=1)                      # a table of every domain, for one step each
+        for i in (ids[0], ids[2]):
+            batch.set_budget(i, 0)
+        batch.step(15)                          # only the resumed domain steps
+        assert batch.status(ids[1]) == (25, 35)
+        for i in (ids[0], ids[2]):
+            batch.set_budget(i, 30)
+        batch.step(40)
+        for i, (f, kw) in zip(ids, jobs):
+            done = batch.status(i)[0]
+            assert done == 60
+            _same(batch.moments(i), _alone(f, done, lattice=19, storage=lbm.LBM_STORE_FP32, **kw))
+    finally:
+        batch.close()
+
+
 def test_batch_d3q19_walls_autotune_and_remove():
     jobs = [
         (W.pool_boiling_3d(nx=40, ny=36, nz=24, depth=8, noise=1e-3, seed=3),

@@ -312,9 +312,10 @@ def storage_leg(storage: int, steps: int, rho_h, u_h, eps_h, stream, dev) -> dic
 
 def slabs_leg(count: int, steps: int, rho_h, u_h, eps_h, stream, dev) -> dict:
     """The headline workload cut into `count` slabs along z on this GPU
-    (lbm_slabs_*): every slab steps, then three halo planes per cut are
-    copied from the neighbours.  Measures what the decomposition costs on one
-    device: the halo planes stepped twice and the copies."""
+    (lbm_slabs_*): every slab collides its owned planes, then each cut's
+    crossing populations and two halo planes per cut side are copied from the
+    neighbours.  Measures what the decomposition costs on one device: the
+    copies, the extra launches and each slab's own partial last wave."""
     import torch
     from paper_1705_10045_gb300 import lbm
     s = lbm.Slabs(count, storage=lbm.LBM_STORE_FP32, device=dev, stream=stream.cuda_stream, **PARAMS)
@@ -333,11 +334,13 @@ def slabs_leg(count: int, steps: int, rho_h, u_h, eps_h, stream, dev) -> dict:
     finally:
         s.close()
     nn = NX * NY * NZ
-    halo = sum(p.lo + p.hi for p in plans)
+    sides = sum((p.lo > 0) + (p.hi > 0) for p in plans)     # halos, one copy of each per round
     plane_bytes = 2 * 19 * 4 * NX * NY
+    crossing_bytes = 2 * 5 * 4 * NX * NY                     # 5 of 19 directions, both sets
     return {"slabs": count, "value": nn / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": steps,
-            "halo_planes_stepped": halo, "halo_bytes_copied_per_step": halo * plane_bytes,
-            "launches_per_step": count + halo // lbm.LBM_SLAB_HALO, "bad_nodes": diag["bad"]}
+            "halo_planes_held": sum(p.lo + p.hi for p in plans), "halo_planes_collided": 0,
+            "bytes_copied_per_step": sides * (lbm.LBM_SLAB_HALO * plane_bytes + crossing_bytes),
+            "launches_per_step": count + 2 * sides, "bad_nodes": diag["bad"]}
 
 
 D2Q9_NX, D2Q9_NY = 8192, 4608

@@ -304,15 +304,20 @@ void lbm_batch_destroy(lbm_batch* b);
  * one step along an axis: the collision of plane c reads the moments and the
  * velocity change du (Sec. 3, force with the stencil of Sec. 3, Eq. (edm))
  * of planes c-1..c+1, du reads Phi one plane further, and the finite
- * differences of Sec. 4 read planes c-1..c+1; so plane c after a step depends
- * on planes c-2..c+2 before it, and with LBM_SLAB_HALO = 3 halo planes beyond
- * each cut every plane a slab owns is computed exactly.  The slab's own
- * boundary treatment beyond its outer halo plane (a wrap, or a wall that the
- * whole domain does not have there) reaches only its two outermost halo
- * planes, which the swap overwrites.  FP64 and FP32 slabs reproduce the
- * undivided domain bit for bit; FP16 slabs key their stochastic rounding by
- * node index within the slab, so they agree in distribution, not in bits. */
-#define LBM_SLAB_HALO 3
+ * differences of Sec. 4 read planes c-1..c+1; so the collision of plane c
+ * depends on planes c-2..c+2, and with LBM_SLAB_HALO = 2 halo planes beyond
+ * each cut every plane a slab owns is collided exactly.  A slab collides its
+ * owned planes only (lbm_set_step_planes); its edge planes push the
+ * populations that cross a cut into its halo planes.  The swap after each
+ * step has two rounds: (1) the crossing populations of each cut (the
+ * directions whose velocity points across it, 5 for D3Q19 and 3 for D2Q9;
+ * lbm_get_crossing / lbm_set_crossing) move from the pushing slab's halo
+ * plane to the owning slab's edge plane; (2) each slab's halo planes are
+ * overwritten with its neighbours' edge planes, complete after round 1.
+ * FP64 and FP32 slabs reproduce the undivided domain bit for bit; FP16 slabs
+ * key their stochastic rounding by node index within the slab, so they agree
+ * in distribution, not in bits. */
+#define LBM_SLAB_HALO 2
 
 typedef struct lbm_slab {
     int first;       /* first plane the slab owns, as an index of the whole domain's last axis */
@@ -347,8 +352,8 @@ lbm_handle* lbm_slabs_domain(lbm_slabs* s, int i);
  * slab is initialised from its own and its halo planes.  Synchronising. */
 int lbm_slabs_init(lbm_slabs* s, const double* rho, const double* u, const double* eps, int mem);
 
-/* n steps: every slab steps once, then every halo is refreshed from the
- * neighbours' owned planes, n times (asynchronous on p->stream). */
+/* n steps: every slab steps once, then the two exchange rounds refresh every
+ * halo, n times (asynchronous on p->stream). */
 int lbm_slabs_step(lbm_slabs* s, int n);
 
 /* As lbm_moments for the whole domain, assembled from the slabs' owned
@@ -381,6 +386,31 @@ size_t lbm_plane_bytes(const lbm_handle* h);
  * last axis. */
 int lbm_get_planes(lbm_handle* h, int first, int count, void* buf, int mem);
 int lbm_set_planes(lbm_handle* h, int first, int count, const void* buf, int mem);
+
+/* Collide only planes [first, first + count) of the last axis in later steps
+ * of the fused step form (a slab's owned planes; count = 0 restores the whole
+ * axis).  The moment and force stages still read the two planes beyond each
+ * end, which must hold valid populations; planes outside the range keep stale
+ * values apart from the pushes of the range's edge planes.  The three-launch
+ * form collides every plane regardless; a slab's exchange overwrites the
+ * planes outside the range either way.  Errors (LBM_ERR_INVALID_ARG): null
+ * handle, range outside the last axis. */
+int lbm_set_step_planes(lbm_handle* h, int first, int count);
+
+/* The populations that cross a cut of the last axis, for the first exchange
+ * round between processes: bytes of one plane's pairs (N_k, g_k) for the
+ * directions whose velocity component along the last axis is +1 (the same
+ * count for -1): 5 directions for D3Q19, 3 for D2Q9. */
+size_t lbm_crossing_bytes(const lbm_handle* h);
+
+/* Copy those pairs of plane `plane` (sign +1 or -1 selects the directions)
+ * out of / into buf, laid out as one row of the plane's nodes per direction
+ * in increasing k, storage format.  mem as for lbm_get_planes (device:
+ * asynchronous on the handle's stream; host: synchronising).  Errors
+ * (LBM_ERR_INVALID_ARG): null pointers, bad mem flag, sign not +1 / -1, no
+ * state yet, plane outside the last axis. */
+int lbm_get_crossing(lbm_handle* h, int plane, int sign, void* buf, int mem);
+int lbm_set_crossing(lbm_handle* h, int plane, int sign, const void* buf, int mem);
 
 /* The paper has no counterpart to this call: it is library plumbing for
  * callers that cannot allocate device memory, either because all their

@@ -76,12 +76,16 @@ template <int Q, typename S, typename R> struct Impl {
         G.na = h->p.nx;
         G.nb = Q == 9 ? 1 : h->p.ny;
         G.nm = Q == 9 ? h->p.ny : h->p.nz;
+        // planes collided (lbm_set_step_planes; all by default)
+        G.m_lo = h->step_count > 0 ? h->step_first : 0;
+        G.m_hi = h->step_count > 0 ? h->step_first + h->step_count : G.nm;
+        const int len = G.m_hi - G.m_lo;
         // planes per CTA: enough CTAs for about two per SM on 152 SMs, and
         // at least 8 planes so that the extra ring planes stay a minority
         const long long tiles = (long long)((G.na + TX - 1) / TX) * ((G.nb + TY - 1) / TY);
-        long long c = (G.nm * tiles + 303) / 304;
+        long long c = (len * tiles + 303) / 304;
         c = c < 8 ? 8 : (c > 64 ? 64 : c);
-        G.chunk = (int)(c > G.nm ? G.nm : c);
+        G.chunk = (int)(c > len ? len : c);
         return G;
     }
 
@@ -95,7 +99,7 @@ template <int Q, typename S, typename R> struct Impl {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             h->fused_ready = true;
         }
-        const dim3 grid((G.na + TX - 1) / TX, (G.nb + TY - 1) / TY, (G.nm + G.chunk - 1) / G.chunk);
+        const dim3 grid((G.na + TX - 1) / TX, (G.nb + TY - 1) / TY, (G.m_hi - G.m_lo + G.chunk - 1) / G.chunk);
         if (h->fault_drop > 0) {   // fault-injection test hook (lbm_test_drop_handoff)
             auto fk = fused_step_fault_kernel<Q, S, R, TX, TY, NP, SPLIT>;
             cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -199,6 +203,8 @@ template <int Q, typename S, typename R> struct Impl {
         // (measured: shorter items for four waves per domain gave 31 instead of
         // 40 jobs/s on the D2Q9 batch and 2.1 instead of 2.4 served jobs/s)
         G.chunk = G.nm < 64 ? G.nm : 64;
+        G.m_lo = 0;
+        G.m_hi = G.nm;
         return G;
     }
 

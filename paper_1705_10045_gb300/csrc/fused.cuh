@@ -103,7 +103,9 @@ template <> struct MVel<19> {
 // Geometry of the march: na x nb tile plane (nb = 1 for D2Q9), nm planes.
 struct MarchGeom {
     int na, nb, nm;
-    int chunk;   // planes per CTA along the march axis
+    int chunk;        // planes per CTA along the march axis
+    int m_lo, m_hi;   // planes whose collision the launch runs (the moment and
+                      // force stages reach two and one planes beyond them)
 };
 
 // Plane buffers: Phi for 3 planes, rho/u/T for 5 planes, du for 4 planes
@@ -536,7 +538,7 @@ __device__ __forceinline__ void fused_tile(const S* __restrict__ src, S* __restr
     st.step = step;
 
     const int tid = threadIdx.x;
-    const int ze = min(zb + G.chunk, G.nm);
+    const int ze = min(zb + G.chunk, G.m_hi);
     const bool walls = p->wall;
     const int wa = p->wall_x, wb = Q == 19 ? p->wall_y : 0;
     for (int i = tid; i < Sh::RW; i += NT) st.ring_a[i] = ring_coord(a0 + i - 2, G.na, wa);
@@ -640,7 +642,8 @@ __global__ void __launch_bounds__(TX* TY + NP, FusedOcc<Q, S>::kMinBlocks)
     fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst, KParams<R> p, MarchGeom G, Counters* cnt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     fused_tile<Q, S, R, TX, TY, NP, false, false, XW, SPLIT>(src, dst, &p, G, p.step, blockIdx.x * TX,
-                                                             blockIdx.y * TY, blockIdx.z * G.chunk, cnt, smem_raw);
+                                                             blockIdx.y * TY, G.m_lo + blockIdx.z * G.chunk, cnt,
+                                                             smem_raw);
 }
 
 // The same step with the fault-injection hook: the first CTA withholds the
@@ -654,8 +657,8 @@ __global__ void __launch_bounds__(TX* TY + NP, FusedOcc<Q, S>::kMinBlocks)
                             int fault_plane) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     fused_tile<Q, S, R, TX, TY, NP, true, false, true, SPLIT>(src, dst, &p, G, p.step, blockIdx.x * TX,
-                                                              blockIdx.y * TY, blockIdx.z * G.chunk, cnt, smem_raw,
-                                                              fault_plane);
+                                                              blockIdx.y * TY, G.m_lo + blockIdx.z * G.chunk, cnt,
+                                                              smem_raw, fault_plane);
 }
 
 // ---------------------------------------------------------------------------

@@ -25,6 +25,8 @@ struct lbm_handle {
     bool initialised = false;
     bool fused_ready = false;   // shared-memory limit of the fused kernel raised
     int fault_drop = 0;         // lbm_test_drop_handoff hook: 1 + plane, 0 = off
+    int step_first = 0;         // lbm_set_step_planes: the fused step collides planes
+    int step_count = 0;         // [step_first, step_first + step_count) of the last axis (0: all)
     cudaStream_t stream = nullptr;
 };
 

@@ -9,20 +9,22 @@
 // div u*), and du of plane c+1 needs Phi of planes c..c+2 (the force of
 // Sec. 3): the post-collision values of plane c depend on the populations of
 // planes c-2..c+2.  Streaming then moves them one plane.  So a slab that
-// holds LBM_SLAB_HALO = 3 copies of its neighbours' planes beyond each cut
-// computes every plane it owns exactly: its halo plane next to the cut
-// depends on planes at most two further out, which it holds, and whatever the
-// slab's own boundary treatment does beyond its last halo plane (a wrap or a
-// wall that is not there in the whole domain) reaches at most the two outer
-// halo planes.  After a step the halo planes are stale; the exchange
-// overwrites all three with the neighbours' new planes, and the slabs need no
-// population-by-population swap across the cut.
+// holds LBM_SLAB_HALO = 2 copies of its neighbours' planes beyond each cut
+// collides every plane it owns exactly; it collides only those
+// (lbm_set_step_planes), and its edge planes push the populations that cross
+// a cut into its halo planes.  After the step the exchange runs in two
+// rounds: (1) each cut's crossing populations (the directions whose velocity
+// points across it: 5 for D3Q19, 3 for D2Q9) go from the pushing slab's halo
+// plane to the owning slab's edge plane, which completes the neighbours'
+// edge planes; (2) each slab's two halo planes are overwritten with those
+// complete edge planes.
 //
-// The cost is 2 x 3 planes recomputed per cut and per step, plus the copies.
-// Every slab uses the same per-node arithmetic as the whole domain, so FP64
-// and FP32 slabs reproduce the undivided domain bit for bit.  FP16 storage
-// keys its stochastic rounding by the node index within a handle, so FP16
-// slabs round differently (same distribution, not the same bits).
+// Per cut and direction that moves 2 Q + (crossing directions) node pairs
+// per node of the plane, and no plane is collided twice.  Every slab uses the
+// same per-node arithmetic as the whole domain, so FP64 and FP32 slabs
+// reproduce the undivided domain bit for bit.  FP16 storage keys its
+// stochastic rounding by the node index within a handle, so FP16 slabs round
+// differently (same distribution, not the same bits).
 #include <cstring>
 #include <new>
 #include <string>
@@ -42,6 +44,7 @@ struct lbm_slabs {
     double* tmp = nullptr;         // (D + 3) field planes of the largest slab
     double* partials = nullptr;    // reduction partials, then kSums results
     long long steps = 0;
+    cudaStream_t main = nullptr;   // the caller's stream, which every slab steps on
 };
 
 namespace {
@@ -98,14 +101,76 @@ int copy_rows(const void* src, long long spitch, void* dst, long long dpitch, lo
     return cuda_error(cudaGetLastError(), "plane copy launch");
 }
 
+// Directions whose velocity component along the last axis is `sign`, in
+// increasing k: the populations a plane pushes across a cut above it (+1) or
+// below it (-1).  Returns how many (5 for D3Q19, 3 for D2Q9).
+int crossing_dirs(int Q, int sign, int* ks) {
+    int n = 0;
+    for (int k = 0; k < Q; ++k) {
+        const int c = Q == 9 ? lbm::Vel<9>::cy(k) : lbm::Vel<19>::cz(k);
+        if (c == sign) ks[n++] = k;
+    }
+    return n;
+}
+
+// up to 8 rows of `width` bytes: src + src[r] -> dst + dst[r], r < gridDim.y
+struct RowTable {
+    long long src[8], dst[8];
+};
+template <typename W>
+__global__ void __launch_bounds__(256) copy_table_kernel(const unsigned char* __restrict__ src,
+                                                         unsigned char* __restrict__ dst, RowTable t,
+                                                         long long words) {
+    const W* s = reinterpret_cast<const W*>(src + t.src[blockIdx.y]);
+    W* d = reinterpret_cast<W*>(dst + t.dst[blockIdx.y]);
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (long long)gridDim.x * blockDim.x)
+        d[w] = s[w];
+}
+
+int copy_table(const void* src, void* dst, const RowTable& t, int rows, long long width, cudaStream_t stream) {
+    if (width <= 0 || rows <= 0) return LBM_OK;
+    unsigned long long all = (unsigned long long)(size_t)src | (unsigned long long)(size_t)dst |
+                             (unsigned long long)width;
+    for (int r = 0; r < rows; ++r) all |= (unsigned long long)t.src[r] | (unsigned long long)t.dst[r];
+    const int wb = (all & 15) == 0 ? 16 : (all & 7) == 0 ? 8 : (all & 3) == 0 ? 4 : 2;
+    const long long words = width / wb;
+    long long bx = (words + 255) / 256;
+    if (bx > 1024) bx = 1024;
+    const dim3 grid((unsigned)bx, (unsigned)rows);
+    const auto* s = static_cast<const unsigned char*>(src);
+    auto* d = static_cast<unsigned char*>(dst);
+    switch (wb) {
+        case 16: copy_table_kernel<uint4><<<grid, 256, 0, stream>>>(s, d, t, words); break;
+        case 8: copy_table_kernel<unsigned long long><<<grid, 256, 0, stream>>>(s, d, t, words); break;
+        case 4: copy_table_kernel<unsigned><<<grid, 256, 0, stream>>>(s, d, t, words); break;
+        default: copy_table_kernel<unsigned short><<<grid, 256, 0, stream>>>(s, d, t, words); break;
+    }
+    return cuda_error(cudaGetLastError(), "crossing copy launch");
+}
+
+// the crossing populations `sign` of plane sp of src's current state into
+// plane dp of dst's
+int copy_crossing(lbm_handle* dst, int dp, const lbm_handle* src, int sp, int sign, cudaStream_t stream) {
+    int ks[8];
+    const int n = crossing_dirs(src->Q, sign, ks);
+    const long long plane = plane_nodes(src->p), e = 2 * (long long)src->elem;
+    RowTable t;
+    for (int j = 0; j < n; ++j) {
+        t.src[j] = (ks[j] * src->nn + sp * plane) * e;
+        t.dst[j] = (ks[j] * dst->nn + dp * plane) * e;
+    }
+    return copy_table(src->pop[src->cur], dst->pop[dst->cur], t, n, plane * e, stream);
+}
+
 // planes [first, first + count) of every population array of the current state
 // (Q arrays of node pairs (N_k, g_k), 2 elem bytes per node)
-int copy_planes(lbm_handle* dst, int dst_first, const lbm_handle* src, int src_first, int count) {
+int copy_planes(lbm_handle* dst, int dst_first, const lbm_handle* src, int src_first, int count,
+                cudaStream_t stream) {
     const long long plane = plane_nodes(src->p);
     const long long e = 2 * (long long)src->elem;
     const auto* s = static_cast<const unsigned char*>(src->pop[src->cur]) + src_first * plane * e;
     auto* d = static_cast<unsigned char*>(dst->pop[dst->cur]) + dst_first * plane * e;
-    return copy_rows(s, src->nn * e, d, dst->nn * e, count * plane * e, src->Q, dst->stream);
+    return copy_rows(s, src->nn * e, d, dst->nn * e, count * plane * e, src->Q, stream);
 }
 
 // Conservation sums of nodes [i0, i0 + n) of a population buffer whose
@@ -204,18 +269,33 @@ int check_slabs(const lbm_slabs* s) {
     return LBM_OK;
 }
 
-// halo planes of every slab from its neighbours' own planes
+// the two rounds of the exchange (see the top of this file), on the caller's stream
 int exchange(lbm_slabs* s) {
     const int H = LBM_SLAB_HALO;
+    // (1) crossing populations: slab i's upper edge plane pushed them into its
+    // halo plane lo + own, its lower edge plane into lo - 1
     for (int i = 0; i < s->count; ++i) {
         const lbm_slab& a = s->plan[i];
         if (a.hi) {
             const lbm_slab& b = s->plan[a.above];
-            if (int rc = copy_planes(s->h[i], a.lo + a.own, s->h[a.above], b.lo, H)) return rc;
+            if (int rc = copy_crossing(s->h[a.above], b.lo, s->h[i], a.lo + a.own, +1, s->main)) return rc;
         }
         if (a.lo) {
             const lbm_slab& b = s->plan[a.below];
-            if (int rc = copy_planes(s->h[i], 0, s->h[a.below], b.lo + b.own - H, H)) return rc;
+            if (int rc = copy_crossing(s->h[a.below], b.lo + b.own - 1, s->h[i], a.lo - 1, -1, s->main))
+                return rc;
+        }
+    }
+    // (2) halo planes from the neighbours' edge planes, now complete
+    for (int i = 0; i < s->count; ++i) {
+        const lbm_slab& a = s->plan[i];
+        if (a.hi) {
+            const lbm_slab& b = s->plan[a.above];
+            if (int rc = copy_planes(s->h[i], a.lo + a.own, s->h[a.above], b.lo, H, s->main)) return rc;
+        }
+        if (a.lo) {
+            const lbm_slab& b = s->plan[a.below];
+            if (int rc = copy_planes(s->h[i], 0, s->h[a.below], b.lo + b.own - H, H, s->main)) return rc;
         }
     }
     return LBM_OK;
@@ -285,6 +365,7 @@ int lbm_slabs_create(const lbm_params* p, int count, lbm_slabs** out) {
     }
     s->p = *p;
     s->count = count;
+    s->main = (cudaStream_t)p->stream;
     s->D = p->lattice == LBM_D2Q9 ? 2 : 3;
     s->plane = plane_nodes(*p);
     s->nn = (long long)p->nx * p->ny * p->nz;
@@ -299,6 +380,9 @@ int lbm_slabs_create(const lbm_params* p, int count, lbm_slabs** out) {
         rc = lbm_create(&sl.p, &h);
         if (rc) break;
         s->h.push_back(h);
+        rc = lbm_set_step_planes(h, sl.lo, sl.own);   // halo planes are refreshed, not collided
+        if (rc) break;
+
         const long long nl = sl.lo + sl.own + sl.hi;
         if (nl > max_nl) max_nl = nl;
     }
@@ -532,6 +616,99 @@ int lbm_set_planes(lbm_handle* h, int first, int count, const void* buf, int mem
         if (int rc = cuda_error(cudaMemcpyAsync(dst + r * h->nn * e, static_cast<const unsigned char*>(buf) + r * width,
                                                 (size_t)width, cudaMemcpyHostToDevice, h->stream),
                                 "plane copy"))
+            return rc;
+    return cuda_error(cudaStreamSynchronize(h->stream), "stream synchronize");
+}
+
+int lbm_set_step_planes(lbm_handle* h, int first, int count) {
+    if (!h) {
+        set_error("lbm_set_step_planes: null handle");
+        return LBM_ERR_INVALID_ARG;
+    }
+    const int nm = last_axis(h->p);
+    if (first < 0 || count < 0 || first + count > nm) {
+        set_error("lbm_set_step_planes: planes outside [0, " + std::to_string(nm) + ")");
+        return LBM_ERR_INVALID_ARG;
+    }
+    h->step_first = count ? first : 0;
+    h->step_count = count;
+    return LBM_OK;
+}
+
+size_t lbm_crossing_bytes(const lbm_handle* h) {
+    if (!h) return 0;
+    int ks[8];
+    return (size_t)crossing_dirs(h->Q, 1, ks) * (size_t)plane_nodes(h->p) * 2 * h->elem;
+}
+
+namespace {
+// checks of lbm_get_crossing / lbm_set_crossing; the row offsets of the
+// plane's crossing pairs in the state and in a packed buffer
+int crossing_rows(lbm_handle* h, int plane, int sign, const void* buf, int mem, const char* who, RowTable& state,
+                  RowTable& packed, int& rows, long long& width) {
+    if (!h || !buf || (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) || (sign != 1 && sign != -1)) {
+        set_error(std::string(who) + ": null handle or buffer, bad mem flag, or sign not +1 / -1");
+        return LBM_ERR_INVALID_ARG;
+    }
+    const int nm = last_axis(h->p);
+    if (!h->initialised || plane < 0 || plane >= nm) {
+        set_error(std::string(who) + ": no state, or plane outside [0, " + std::to_string(nm) + ")");
+        return LBM_ERR_INVALID_ARG;
+    }
+    int ks[8];
+    rows = crossing_dirs(h->Q, sign, ks);
+    const long long pn = plane_nodes(h->p), e = 2 * (long long)h->elem;
+    width = pn * e;
+    for (int j = 0; j < rows; ++j) {
+        state.src[j] = state.dst[j] = (ks[j] * h->nn + plane * pn) * e;
+        packed.src[j] = packed.dst[j] = j * width;
+    }
+    return LBM_OK;
+}
+}  // namespace
+
+int lbm_get_crossing(lbm_handle* h, int plane, int sign, void* buf, int mem) {
+    RowTable st, pk;
+    int rows = 0;
+    long long width = 0;
+    if (int rc = crossing_rows(h, plane, sign, buf, mem, "lbm_get_crossing", st, pk, rows, width)) return rc;
+    DeviceGuard dg(h->p.device);
+    const auto* src = static_cast<const unsigned char*>(h->pop[h->cur]);
+    if (mem == LBM_MEM_DEVICE) {
+        RowTable t;
+        for (int j = 0; j < rows; ++j) {
+            t.src[j] = st.src[j];
+            t.dst[j] = pk.dst[j];
+        }
+        return copy_table(src, buf, t, rows, width, h->stream);
+    }
+    for (int j = 0; j < rows; ++j)
+        if (int rc = cuda_error(cudaMemcpyAsync(static_cast<unsigned char*>(buf) + pk.dst[j], src + st.src[j],
+                                                (size_t)width, cudaMemcpyDeviceToHost, h->stream),
+                                "crossing copy"))
+            return rc;
+    return cuda_error(cudaStreamSynchronize(h->stream), "stream synchronize");
+}
+
+int lbm_set_crossing(lbm_handle* h, int plane, int sign, const void* buf, int mem) {
+    RowTable st, pk;
+    int rows = 0;
+    long long width = 0;
+    if (int rc = crossing_rows(h, plane, sign, buf, mem, "lbm_set_crossing", st, pk, rows, width)) return rc;
+    DeviceGuard dg(h->p.device);
+    auto* dst = static_cast<unsigned char*>(h->pop[h->cur]);
+    if (mem == LBM_MEM_DEVICE) {
+        RowTable t;
+        for (int j = 0; j < rows; ++j) {
+            t.src[j] = pk.src[j];
+            t.dst[j] = st.dst[j];
+        }
+        return copy_table(buf, dst, t, rows, width, h->stream);
+    }
+    for (int j = 0; j < rows; ++j)
+        if (int rc = cuda_error(cudaMemcpyAsync(dst + st.dst[j], static_cast<const unsigned char*>(buf) + pk.src[j],
+                                                (size_t)width, cudaMemcpyHostToDevice, h->stream),
+                                "crossing copy"))
             return rc;
     return cuda_error(cudaStreamSynchronize(h->stream), "stream synchronize");
 }

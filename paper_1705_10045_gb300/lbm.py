@@ -46,8 +46,9 @@ EXPORTED = ("lbm_default_params", "lbm_create", "lbm_init", "lbm_step", "lbm_mom
             "lbm_batch_destroy", "lbm_conservation_sums_noalloc", "lbm_coexistence", "lbm_slab_plan",
             "lbm_slabs_create", "lbm_slabs_count", "lbm_slabs_domain", "lbm_slabs_init", "lbm_slabs_step",
             "lbm_slabs_moments", "lbm_slabs_diagnostics", "lbm_slabs_sync", "lbm_slabs_destroy", "lbm_plane_bytes",
-            "lbm_get_planes", "lbm_set_planes", "lbm_moments_f")
-LBM_SLAB_HALO = 3
+            "lbm_get_planes", "lbm_set_planes", "lbm_moments_f", "lbm_set_step_planes", "lbm_crossing_bytes",
+            "lbm_get_crossing", "lbm_set_crossing")
+LBM_SLAB_HALO = 2
 
 
 class LbmError(RuntimeError):
@@ -170,9 +171,14 @@ def load(path: str = LIB_PATH):
     lib.lbm_plane_bytes.restype = ctypes.c_size_t
     lib.lbm_get_planes.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     lib.lbm_set_planes.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    lib.lbm_set_step_planes.argtypes = [H, ctypes.c_int, ctypes.c_int]
+    lib.lbm_crossing_bytes.argtypes = [H]
+    lib.lbm_crossing_bytes.restype = ctypes.c_size_t
+    lib.lbm_get_crossing.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    lib.lbm_set_crossing.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     for name in ("lbm_slab_plan", "lbm_slabs_create", "lbm_slabs_count", "lbm_slabs_init", "lbm_slabs_step",
                  "lbm_slabs_moments", "lbm_slabs_diagnostics", "lbm_slabs_sync", "lbm_get_planes",
-                 "lbm_set_planes"):
+                 "lbm_set_planes", "lbm_set_step_planes", "lbm_get_crossing", "lbm_set_crossing"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_status",
                  "lbm_batch_set_budget", "lbm_batch_size", "lbm_batch_variants", "lbm_batch_set_variant",
@@ -382,9 +388,9 @@ def lbm_plane_bytes(h) -> int:
 
 
 def lbm_get_planes(h, first: int, count: int, buf):
-    """Planes [first, first + count) of the populations into buf (2Q rows of
-    `count` planes, storage format); device buffers are filled asynchronously
-    on the handle's stream."""
+    """Planes [first, first + count) of the populations into buf (Q rows of
+    `count` planes of (N_k, g_k) pairs, storage format); device buffers are
+    filled asynchronously on the handle's stream."""
     a, mem, n = _byte_addr(buf)
     if n < count * lbm_plane_bytes(h):
         raise ValueError("plane buffer too small")
@@ -396,6 +402,31 @@ def lbm_set_planes(h, first: int, count: int, buf):
     if n < count * lbm_plane_bytes(h):
         raise ValueError("plane buffer too small")
     return _check(load().lbm_set_planes(h, int(first), int(count), a, mem))
+
+
+def lbm_set_step_planes(h, first: int, count: int):
+    """Collide only planes [first, first + count) of the last axis (0: all)."""
+    return _check(load().lbm_set_step_planes(h, int(first), int(count)))
+
+
+def lbm_crossing_bytes(h) -> int:
+    return int(load().lbm_crossing_bytes(h))
+
+
+def lbm_get_crossing(h, plane: int, sign: int, buf):
+    """The pairs of plane `plane` for the directions whose last-axis velocity
+    component is `sign` (+1 / -1) into buf (one row per direction)."""
+    a, mem, n = _byte_addr(buf)
+    if n < lbm_crossing_bytes(h):
+        raise ValueError("crossing buffer too small")
+    return _check(load().lbm_get_crossing(h, int(plane), int(sign), a, mem))
+
+
+def lbm_set_crossing(h, plane: int, sign: int, buf):
+    a, mem, n = _byte_addr(buf)
+    if n < lbm_crossing_bytes(h):
+        raise ValueError("crossing buffer too small")
+    return _check(load().lbm_set_crossing(h, int(plane), int(sign), a, mem))
 
 
 class Lbm:

@@ -1,18 +1,22 @@
 """One domain over several processes: rank r holds slab r of the cut along
-the last axis (``lbm_slab_plan``) and swaps halo planes with its neighbours
-through ``torch.distributed`` after every step.
+the last axis (``lbm_slab_plan``) and swaps halos with its neighbours through
+``torch.distributed`` after every step.
 
-The plan, the halo depth and the reason three planes suffice are the
-library's (``lbm_slab_plan`` in include/lbm.h): a step moves information two
-planes for the force and finite-difference stencils plus one for streaming,
-so a slab whose three halo planes beyond each cut are refreshed after every
-step computes every plane it owns exactly as the undivided domain would.
+The plan, the halo depth and the exchange are the library's (``lbm_slab_plan``
+and the slab notes in include/lbm.h): the collision of a plane reads the
+populations of the two planes beyond it on either side, so a slab with two
+halo planes beyond each cut collides every plane it owns exactly and collides
+only those.  After a step its edge planes have pushed the populations that
+cross a cut into its halo planes; the swap moves them to the neighbour that
+owns their plane (round 1), then refreshes the halo planes from the
+neighbours' edge planes, which round 1 has completed (round 2).
 
-``exchange_halos`` is the swap itself, written against two callables that
-read and write planes of a slab, so that it does not care where the planes
-live.  ``SlabRank`` binds it to a library handle on this process's GPU: NCCL
-moves the device buffers; a gloo group gets them staged through host memory.  Only a process group is needed: the swap is
-point-to-point (no collective on the data path).
+``exchange_halos`` is the swap itself, written against callables that read
+and write planes and crossing populations of a slab, so that it does not care
+where they live.  ``SlabRank`` binds it to a library handle on this process's
+GPU: NCCL moves the device buffers; a gloo group gets them staged through host
+memory.  Only a process group is needed: the swap is point-to-point (no
+collective on the data path).
 """
 from __future__ import annotations
 
@@ -20,38 +24,64 @@ import numpy as np
 
 from . import lbm
 
-# tags of the two messages a rank sends per step: its top owned planes
-# travelling up and its bottom owned planes travelling down (with two slabs of
-# a periodic domain both go to the same peer)
-TAG_UP, TAG_DOWN = 0, 1
+# tags of the messages a rank sends per step: crossing populations and edge
+# planes travelling up and down (with two slabs of a periodic domain both
+# directions go to the same peer)
+TAG_CROSS_UP, TAG_CROSS_DOWN, TAG_UP, TAG_DOWN = 0, 1, 2, 3
 
 
-def exchange_halos(dist, slab, get, put, group=None):
-    """Refresh the halo planes of `slab` (an ``lbm_slab``; this rank holds
-    slab index == rank) from its neighbours.  ``get(first, count)`` returns a
-    contiguous tensor of the local planes [first, first + count);
-    ``put(first, count, tensor)`` stores one.  Sends are posted with the
-    receives in one batch, so no pair of ranks can wait on each other."""
-    H = lbm.LBM_SLAB_HALO
-    ops, recvs = [], []
-    up = get(slab.lo + slab.own - H, H) if slab.hi else None
-    down = get(slab.lo, H) if slab.lo else None
-    if up is not None:
-        ops.append(dist.P2POp(dist.isend, up, slab.above, group, TAG_UP))
-    if down is not None:
-        ops.append(dist.P2POp(dist.isend, down, slab.below, group, TAG_DOWN))
-    if down is not None:
-        buf = down.new_empty(down.shape)
-        ops.append(dist.P2POp(dist.irecv, buf, slab.below, group, TAG_UP))
-        recvs.append((0, buf))
-    if up is not None:
-        buf = up.new_empty(up.shape)
-        ops.append(dist.P2POp(dist.irecv, buf, slab.above, group, TAG_DOWN))
-        recvs.append((slab.lo + slab.own, buf))
+def _swap(dist, group, sends, recvs):
+    """Post every send with every receive in one batch (no pair of ranks can
+    wait on each other) and wait for all of them."""
+    ops = [dist.P2POp(dist.isend, t, peer, group, tag) for t, peer, tag in sends]
+    ops += [dist.P2POp(dist.irecv, t, peer, group, tag) for t, peer, tag in recvs]
     if ops:
         for req in dist.batch_isend_irecv(ops):
             req.wait()
-    for first, buf in recvs:
+
+
+def exchange_halos(dist, slab, get, put, get_cross, put_cross, group=None):
+    """Refresh the halos of `slab` (an ``lbm_slab``; this rank holds slab
+    index == rank) from its neighbours after a step.  ``get(first, count)``
+    returns a contiguous tensor of the local planes [first, first + count),
+    ``put(first, count, tensor)`` stores one; ``get_cross(plane, sign)`` and
+    ``put_cross(plane, sign, tensor)`` do the same for the populations of
+    one plane whose velocity has last-axis component ``sign``."""
+    H = lbm.LBM_SLAB_HALO
+    top, bottom = slab.lo + slab.own - 1, slab.lo      # edge planes
+    # round 1: what the edge planes pushed into the halo planes goes to its owner
+    sends, recvs, puts = [], [], []
+    if slab.hi:
+        sends.append((get_cross(top + 1, +1), slab.above, TAG_CROSS_UP))
+    if slab.lo:
+        sends.append((get_cross(bottom - 1, -1), slab.below, TAG_CROSS_DOWN))
+    if slab.lo:
+        buf = sends[-1][0].new_empty(sends[-1][0].shape)
+        recvs.append((buf, slab.below, TAG_CROSS_UP))
+        puts.append((bottom, +1, buf))
+    if slab.hi:
+        buf = sends[0][0].new_empty(sends[0][0].shape)
+        recvs.append((buf, slab.above, TAG_CROSS_DOWN))
+        puts.append((top, -1, buf))
+    _swap(dist, group, sends, recvs)
+    for plane, sign, buf in puts:
+        put_cross(plane, sign, buf)
+    # round 2: the halo planes from the neighbours' edge planes, now complete
+    sends, recvs, puts = [], [], []
+    if slab.hi:
+        sends.append((get(top + 1 - H, H), slab.above, TAG_UP))
+    if slab.lo:
+        sends.append((get(bottom, H), slab.below, TAG_DOWN))
+    if slab.lo:
+        buf = sends[-1][0].new_empty(sends[-1][0].shape)
+        recvs.append((buf, slab.below, TAG_UP))
+        puts.append((0, buf))
+    if slab.hi:
+        buf = sends[0][0].new_empty(sends[0][0].shape)
+        recvs.append((buf, slab.above, TAG_DOWN))
+        puts.append((top + 1, buf))
+    _swap(dist, group, sends, recvs)
+    for first, buf in puts:
         put(first, H, buf)
 
 
@@ -79,9 +109,12 @@ class SlabRank:
         self.params = lbm.make_params(**kw)
         self.slab = lbm.lbm_slab_plan(self.params, self.world, self.rank)
         self.h = lbm.lbm_create(self.slab.p)
+        if self.world > 1:   # halo planes are refreshed, not collided
+            lbm.lbm_set_step_planes(self.h, self.slab.lo, self.slab.own)
         self.d = 2 if self.params.lattice == lbm.LBM_D2Q9 else 3
         self.nm = self.params.ny if self.params.lattice == lbm.LBM_D2Q9 else self.params.nz
         self.plane_bytes = lbm.lbm_plane_bytes(self.h)
+        self.cross_bytes = lbm.lbm_crossing_bytes(self.h)
         self.device = torch.device("cuda", torch.cuda.current_device())
         # gloo moves host tensors only: stage the planes through host memory
         self.staging = torch.device("cpu") if dist.get_backend(group) == "gloo" else self.device
@@ -106,10 +139,20 @@ class SlabRank:
     def _put(self, first, count, buf):
         lbm.lbm_set_planes(self.h, first, count, buf)
 
+    def _get_cross(self, plane, sign):
+        import torch
+        buf = torch.empty(self.cross_bytes, dtype=torch.uint8, device=self.staging)
+        lbm.lbm_get_crossing(self.h, plane, sign, buf)
+        return buf
+
+    def _put_cross(self, plane, sign, buf):
+        lbm.lbm_set_crossing(self.h, plane, sign, buf)
+
     def step(self, n: int = 1):
         for _ in range(int(n)):
             lbm.lbm_step(self.h, 1)
-            exchange_halos(self.dist, self.slab, self._get, self._put, self.group)
+            exchange_halos(self.dist, self.slab, self._get, self._put, self._get_cross, self._put_cross,
+                           self.group)
 
     def moments(self) -> dict:
         """rho, u*, T, P of the planes this rank owns (host arrays)."""

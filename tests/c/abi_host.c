@@ -31,7 +31,7 @@ int main(void) {
     rc = lbm_slab_plan(&p, 3, 1, &s);
     printf("slab %d %d %d %d %d %d %d %d %d\n", rc, s.first, s.own, s.lo, s.hi, s.below, s.above, s.p.nz,
            s.p.T_fixed_lo);
-    rc = lbm_slab_plan(&p, 20, 0, &s);
+    rc = lbm_slab_plan(&p, 21, 0, &s);
     printf("slab_thin %d %s\n", rc, strlen(lbm_last_error()) > 0 ? "msg" : "nomsg");
 
     lbm_handle* h = NULL;

@@ -58,8 +58,9 @@ def test_host_calls_from_c(program):
     assert float(rv) == pytest.approx(0.239666921841, abs=1e-9)
     assert float(rl) == pytest.approx(1.93270582860, abs=1e-9)
     assert program["coexistence_bad"] == [str(lbm.LBM_ERR_INVALID_ARG)]
-    # 40 planes into 3 slabs: 14, 13, 13; slab 1 owns [14, 27) with halos on both cuts
-    assert program["slab"] == ["0", "14", "13", "3", "3", "0", "2", "19", "0"]
+    # 40 planes into 3 slabs: 14, 13, 13; slab 1 owns [14, 27) with two halo
+    # planes at both cuts; 40 planes into 21 slabs would own 1 plane, too thin
+    assert program["slab"] == ["0", "14", "13", "2", "2", "0", "2", "17", "0"]
     assert program["slab_thin"] == [str(lbm.LBM_ERR_INVALID_ARG), "msg"]
     assert program["create_bad"] == [str(lbm.LBM_ERR_INVALID_ARG), "null"]
     assert program["null_step"] == [str(lbm.LBM_ERR_INVALID_ARG)]

@@ -1,6 +1,8 @@
-"""Slabs on the GPU (lbm_slabs_*, lbm_get_planes / lbm_set_planes, SlabRank):
-one domain cut along its last axis into slabs that swap three halo planes
-after every step.
+"""Slabs on the GPU (lbm_slabs_*, lbm_get_planes / lbm_set_planes,
+lbm_get_crossing / lbm_set_crossing, lbm_set_step_planes, SlabRank): one
+domain cut along its last axis into slabs that collide their owned planes
+and, after every step, swap the populations crossing each cut and then two
+halo planes.
 
 * FP32 and FP64 slabs reproduce the undivided domain bit for bit (same
   per-node arithmetic), for 1 to 4 slabs, walls with a heated floor, latent
@@ -10,8 +12,8 @@ after every step.
 * FP16 slabs round with their own node keys: within the FP16 bounds of the
   undivided run (the bounds of test_gpu_precision.py).
 * The sums over the owned planes equal the undivided domain's to rounding.
-* Plane copies round-trip through host and device buffers and reject planes
-  outside the slab.
+* Plane and crossing copies round-trip through host and device buffers and
+  reject planes outside the slab; step ranges outside the axis are refused.
 * Two processes on the same GPU, one slab each (SlabRank over gloo with host
   staging), reproduce the undivided domain bit for bit.
 """
@@ -151,6 +153,53 @@ def test_plane_copies_round_trip_through_host_and_device_buffers():
             for bad in ((38, 3), (-1, 2), (0, 41)):
                 with pytest.raises(lbm.LbmError) as e:
                     lbm.lbm_get_planes(a.h, bad[0], bad[1], np.empty(max(bad[1], 1) * pb, dtype=np.uint8))
+                assert e.value.code == lbm.LBM_ERR_INVALID_ARG
+        finally:
+            a.close()
+            b.close()
+
+
+def test_crossing_copies_round_trip_and_reject_bad_arguments():
+    import torch
+    f, kw, _ = _walled3d()
+    for storage in (lbm.LBM_STORE_FP64, lbm.LBM_STORE_FP32, lbm.LBM_STORE_FP16):
+        a = lbm.Lbm(**dict(kw, storage=storage))
+        b = lbm.Lbm(**dict(kw, storage=storage))
+        try:
+            a.init(f.rho, np.ascontiguousarray(f.u), 1.5 * f.T)
+            b.init(np.full_like(f.rho, 0.5), np.zeros_like(f.u), np.full_like(f.T, 1.2))
+            a.step(3)
+            cb = lbm.lbm_crossing_bytes(a.h)
+            assert cb == 5 * 32 * 24 * 2 * {0: 8, 1: 4, 2: 2}[storage]
+            for sign in (1, -1):
+                host = np.empty(cb, dtype=np.uint8)
+                lbm.lbm_get_crossing(a.h, 17, sign, host)
+                dev = torch.empty(cb, dtype=torch.uint8, device="cuda")
+                lbm.lbm_get_crossing(a.h, 17, sign, dev)
+                lbm.lbm_sync(a.h)
+                assert np.array_equal(host, dev.cpu().numpy())
+                lbm.lbm_set_crossing(b.h, 5, sign, dev)
+                back = np.empty(cb, dtype=np.uint8)
+                lbm.lbm_get_crossing(b.h, 5, sign, back)
+                assert np.array_equal(back, host)
+            # the crossing rows are rows of the plane copy: direction k's row
+            pb = lbm.lbm_plane_bytes(a.h) // 19
+            plane = np.empty(19 * pb, dtype=np.uint8)
+            lbm.lbm_get_planes(a.h, 17, 1, plane)
+            host = np.empty(cb, dtype=np.uint8)
+            lbm.lbm_get_crossing(a.h, 17, 1, host)
+            sys.path.insert(0, ROOT)
+            import oracle
+            up = np.flatnonzero(oracle.lattice(19)["c"][:, 2] == 1)   # directions with c_z = +1
+            assert len(up) == 5
+            assert np.array_equal(host, np.concatenate([plane[k * pb:(k + 1) * pb] for k in up]))
+            for bad in ((40, 1), (-1, 1), (3, 0), (3, 2)):
+                with pytest.raises(lbm.LbmError) as e:
+                    lbm.lbm_get_crossing(a.h, bad[0], bad[1], np.empty(cb, dtype=np.uint8))
+                assert e.value.code == lbm.LBM_ERR_INVALID_ARG
+            for bad in ((-1, 3), (30, 11), (0, -1)):
+                with pytest.raises(lbm.LbmError) as e:
+                    lbm.lbm_set_step_planes(a.h, *bad)
                 assert e.value.code == lbm.LBM_ERR_INVALID_ARG
         finally:
             a.close()

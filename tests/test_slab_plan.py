@@ -61,19 +61,21 @@ def test_one_slab_is_the_whole_domain():
 
 @pytest.mark.parametrize("count, i", [(0, 0), (2, 2), (2, -1), (4, 0)])
 def test_plan_rejects_bad_counts_and_thin_slabs(count, i):
-    # 14 planes into 4 slabs would leave slabs of 3 and 4 planes: allowed;
-    # 11 planes into 4 would leave 2-plane slabs, thinner than the halo
-    p = lbm.make_params(lattice=19, nx=4, ny=4, nz=11)
+    # 8 planes into 4 slabs leaves slabs of 2 planes, as many as the halo
+    # (a neighbour's halo copies both): allowed; 7 planes into 4 would leave
+    # 1-plane slabs, thinner than the halo
+    assert H == 2
+    p = lbm.make_params(lattice=19, nx=4, ny=4, nz=7)
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_slab_plan(p, count, i)
     assert e.value.code == lbm.LBM_ERR_INVALID_ARG
-    assert lbm.lbm_slab_plan(lbm.make_params(lattice=19, nx=4, ny=4, nz=14), 4, 3).own == 3
+    assert lbm.lbm_slab_plan(lbm.make_params(lattice=19, nx=4, ny=4, nz=8), 4, 3).own == 2
 
 
 @pytest.mark.parametrize("count", [0, -1, 5])
 def test_slabs_create_rejects_bad_counts_before_touching_a_device(count):
     import ctypes
-    p = lbm.make_params(lattice=19, nx=4, ny=4, nz=11)
+    p = lbm.make_params(lattice=19, nx=4, ny=4, nz=9)
     s = ctypes.c_void_p()
     assert lbm.load().lbm_slabs_create(ctypes.byref(p), count, ctypes.byref(s)) == lbm.LBM_ERR_INVALID_ARG
     assert not s.value

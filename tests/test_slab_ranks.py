@@ -2,12 +2,15 @@
 domain (the plan of lbm_slab_plan) with the FP64 oracle as the per-slab
 step, and swap halos with exchange_halos after every step.  The owned planes,
 put back together, must equal the undivided oracle run bit for bit: this
-checks the halo depth (three planes per cut), the neighbour and tag pairing
-of the swap, the periodic wrap and the treatment of the cut ends (fixed wall
-temperatures only at the domain's walls) independently of the GPU.  A rank
-that leaves between steps, or stays but withholds its halo, makes its
-neighbour's swap fail (at once, or after the process group's timeout)
-instead of hanging."""
+checks the halo depth (two planes per cut), the two exchange rounds (the
+populations that cross a cut, then the halo planes), the neighbour and tag
+pairing of the swap, the periodic wrap and the treatment of the cut ends
+(fixed wall temperatures only at the domain's walls) independently of the
+GPU.  The oracle collides its halo planes too; their pushes across the cut
+are wrong (a halo plane lacks the planes beyond it), and round 1 must replace
+them: without it the run differs.  A rank that leaves between steps, or stays
+but withholds its halo, makes its neighbour's swap fail (at once, or after
+the process group's timeout) instead of hanging."""
 import datetime
 import os
 import socket
@@ -64,7 +67,7 @@ def _plane_view(a, Q, first, count):
     return a[:, first:first + count] if Q == 19 else a[:, :, first:first + count]
 
 
-def _rank(rank, world, port, case, out, leave_after, withhold_at=None, timeout_s=20):
+def _rank(rank, world, port, case, out, leave_after, withhold_at=None, timeout_s=20, skip_round1=False):
     sys.path.insert(0, ROOT)
     import torch
     import torch.distributed as dist
@@ -95,6 +98,23 @@ def _rank(rank, world, port, case, out, leave_after, withhold_at=None, timeout_s
             _plane_view(st.N, Q, first, count)[...] = a[:Q]
             _plane_view(st.g, Q, first, count)[...] = a[Q:]
 
+        # directions whose velocity component along the last axis is +1 / -1,
+        # from the oracle's own velocity table
+        c_last = oracle.lattice(Q)["c"][:, 2 if Q == 19 else 1]
+        dirs = {sgn: np.flatnonzero(c_last == sgn) for sgn in (1, -1)}
+
+        def get_cross(plane, sgn):
+            k = dirs[sgn]
+            return torch.from_numpy(np.ascontiguousarray(np.concatenate(
+                [_plane_view(st.N, Q, plane, 1)[k], _plane_view(st.g, Q, plane, 1)[k]])))
+
+        def put_cross(plane, sgn, t):
+            if skip_round1:
+                return
+            a, k = t.numpy(), dirs[sgn]
+            _plane_view(st.N, Q, plane, 1)[k] = a[:len(k)]
+            _plane_view(st.g, Q, plane, 1)[k] = a[len(k):]
+
         for s in range(cfg["steps"]):
             if leave_after is not None and rank == world - 1 and s == leave_after:
                 out[rank] = "left"
@@ -105,7 +125,7 @@ def _rank(rank, world, port, case, out, leave_after, withhold_at=None, timeout_s
                 return
             st.step(1)
             try:
-                exchange_halos(dist, slab, get, put)
+                exchange_halos(dist, slab, get, put, get_cross, put_cross)
             except RuntimeError as e:
                 out[rank] = ("failed", s, str(e)[:200])
                 return
@@ -141,6 +161,31 @@ def test_slabs_on_gloo_ranks_equal_the_undivided_oracle_bit_for_bit(case):
     # the run moved: the state is not the initial one
     init = oracle.State(_oracle_params(whole), *_fields(cfg["p"]))
     assert not np.array_equal(init.N, ref.N)
+
+
+@pytest.mark.parametrize("case", ["d2q9_walls_3", "d3q19_periodic_3"])
+def test_without_the_crossing_round_the_slabs_differ(case):
+    """Negative control: the same runs with round 1 skipped (the halo planes'
+    own, incomplete pushes across the cut kept) do not reproduce the
+    undivided oracle."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1705_10045_gb300 import lbm
+    cfg = CASES[case]
+    world = cfg["world"]
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, _free_port(), case, out, None, None, 20, True), nprocs=world, join=True)
+        got = dict(out)
+    whole = lbm.make_params(**cfg["p"])
+    Q = whole.lattice
+    ref = oracle.State(_oracle_params(whole), *_fields(cfg["p"]))
+    ref.step(cfg["steps"])
+    diff = 0.0
+    for r in range(world):
+        first, own, n, e = got[r]
+        diff = max(diff, np.abs(n - _plane_view(ref.N, Q, first, own)).max())
+    assert diff > 1e-12
 
 
 def test_a_rank_that_leaves_makes_its_neighbours_swap_fail_not_hang():

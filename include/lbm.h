@@ -406,7 +406,13 @@ size_t lbm_crossing_bytes(const lbm_handle* h);
 /* Copy those pairs of plane `plane` (sign +1 or -1 selects the directions)
  * out of / into buf, laid out as one row of the plane's nodes per direction
  * in increasing k, storage format.  mem as for lbm_get_planes (device:
- * asynchronous on the handle's stream; host: synchronising).  Errors
+ * asynchronous on the handle's stream; host: synchronising).  With walls on
+ * x (or on y of D3Q19), lbm_set_crossing leaves alone the wall column (row)
+ * of each direction whose velocity points away from that wall: no node
+ * pushes those populations across the cut (they would come from beyond the
+ * wall); the receiving node's own bounce-back wrote them in its step.  With
+ * such walls and a host buffer, or a device buffer not aligned to a pair, it
+ * stages the rows in the handle's idle population buffer.  Errors
  * (LBM_ERR_INVALID_ARG): null pointers, bad mem flag, sign not +1 / -1, no
  * state yet, plane outside the last axis. */
 int lbm_get_crossing(lbm_handle* h, int plane, int sign, void* buf, int mem);

@@ -148,8 +148,70 @@ int copy_table(const void* src, void* dst, const RowTable& t, int rows, long lon
     return cuda_error(cudaGetLastError(), "crossing copy launch");
 }
 
+// Crossing populations beside a wall across the plane.  A population that
+// arrives at a cut's edge plane moving away from a wall on x (or on y of
+// D3Q19) would come from a node beyond that wall: no slab pushes it.  The
+// receiving node's own bounce-back wrote it in the receiving slab's step, and
+// the pushing slab's halo slot holds no value of this step.  So round 1 skips,
+// per direction, the column x = 0 (c_x = +1) or x = nx - 1 (c_x = -1) across
+// a wall on x, and the row y = 0 or ny - 1 across a wall on y.  -1: no skip.
+struct CrossSkip {
+    int x[8], y[8];
+};
+
+// the skips of the crossing directions ks[0..n) of a plane of `p`; false when
+// there are none (no walls across the plane)
+bool crossing_skips(const lbm_params& p, const int* ks, int n, CrossSkip& sk) {
+    bool any = false;
+    for (int j = 0; j < n; ++j) {
+        const int cx = p.lattice == LBM_D2Q9 ? lbm::Vel<9>::cx(ks[j]) : lbm::Vel<19>::cx(ks[j]);
+        const int cy = p.lattice == LBM_D2Q9 ? 0 : lbm::Vel<19>::cy(ks[j]);
+        sk.x[j] = p.wall_x && cx ? (cx > 0 ? 0 : p.nx - 1) : -1;
+        sk.y[j] = p.lattice == LBM_D3Q19 && p.wall_y && cy ? (cy > 0 ? 0 : p.ny - 1) : -1;
+        any = any || sk.x[j] >= 0 || sk.y[j] >= 0;
+    }
+    return any;
+}
+
+// rows j < gridDim.y of node pairs P: pair n of a plane (x = n mod nx,
+// y = n / nx) from src + t.src[j] to dst + t.dst[j], except column sk.x[j] and
+// row sk.y[j]
+template <typename P>
+__global__ void __launch_bounds__(256) crossing_kernel(const unsigned char* __restrict__ src,
+                                                       unsigned char* __restrict__ dst, RowTable t, CrossSkip sk,
+                                                       long long plane, int nx) {
+    const P* s = reinterpret_cast<const P*>(src + t.src[blockIdx.y]);
+    P* d = reinterpret_cast<P*>(dst + t.dst[blockIdx.y]);
+    const int sx = sk.x[blockIdx.y];
+    const long long sy = sk.y[blockIdx.y];
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < plane;
+         n += (long long)gridDim.x * blockDim.x) {
+        const long long y = n / nx;
+        if ((int)(n - y * nx) == sx || y == sy) continue;
+        d[n] = s[n];
+    }
+}
+
+// crossing rows with wall skips; every address and offset must be a multiple
+// of the pair size (2 elem bytes)
+int copy_crossing_rows(const void* src, void* dst, const RowTable& t, const CrossSkip& sk, int rows,
+                       long long plane, int nx, int elem, cudaStream_t stream) {
+    if (plane <= 0 || rows <= 0) return LBM_OK;
+    long long bx = (plane + 255) / 256;
+    if (bx > 1024) bx = 1024;
+    const dim3 grid((unsigned)bx, (unsigned)rows);
+    const auto* s = static_cast<const unsigned char*>(src);
+    auto* d = static_cast<unsigned char*>(dst);
+    switch (2 * elem) {
+        case 16: crossing_kernel<uint4><<<grid, 256, 0, stream>>>(s, d, t, sk, plane, nx); break;
+        case 8: crossing_kernel<unsigned long long><<<grid, 256, 0, stream>>>(s, d, t, sk, plane, nx); break;
+        default: crossing_kernel<unsigned><<<grid, 256, 0, stream>>>(s, d, t, sk, plane, nx); break;
+    }
+    return cuda_error(cudaGetLastError(), "crossing copy launch");
+}
+
 // the crossing populations `sign` of plane sp of src's current state into
-// plane dp of dst's
+// plane dp of dst's (walls across the plane: the wall skips above)
 int copy_crossing(lbm_handle* dst, int dp, const lbm_handle* src, int sp, int sign, cudaStream_t stream) {
     int ks[8];
     const int n = crossing_dirs(src->Q, sign, ks);
@@ -159,6 +221,10 @@ int copy_crossing(lbm_handle* dst, int dp, const lbm_handle* src, int sp, int si
         t.src[j] = (ks[j] * src->nn + sp * plane) * e;
         t.dst[j] = (ks[j] * dst->nn + dp * plane) * e;
     }
+    CrossSkip sk;
+    if (crossing_skips(dst->p, ks, n, sk))
+        return copy_crossing_rows(src->pop[src->cur], dst->pop[dst->cur], t, sk, n, plane, dst->p.nx, dst->elem,
+                                  stream);
     return copy_table(src->pop[src->cur], dst->pop[dst->cur], t, n, plane * e, stream);
 }
 
@@ -697,6 +763,32 @@ int lbm_set_crossing(lbm_handle* h, int plane, int sign, const void* buf, int me
     if (int rc = crossing_rows(h, plane, sign, buf, mem, "lbm_set_crossing", st, pk, rows, width)) return rc;
     DeviceGuard dg(h->p.device);
     auto* dst = static_cast<unsigned char*>(h->pop[h->cur]);
+    int ks[8];
+    CrossSkip sk;
+    crossing_dirs(h->Q, sign, ks);
+    if (crossing_skips(h->p, ks, rows, sk)) {
+        // walls across the plane: the rows go through the wall-skipping copy,
+        // from the caller's device buffer if it is aligned to a pair, else
+        // staged in the idle population buffer (free between steps)
+        const long long e = 2 * (long long)h->elem;
+        const void* from = buf;
+        if (mem == LBM_MEM_HOST || ((unsigned long long)(size_t)buf % (unsigned long long)e) != 0) {
+            auto* stage = static_cast<unsigned char*>(h->pop[h->cur ^ 1]);
+            const cudaMemcpyKind kind = mem == LBM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+            if (int rc = cuda_error(cudaMemcpyAsync(stage, buf, (size_t)(rows * width), kind, h->stream),
+                                    "crossing copy"))
+                return rc;
+            from = stage;
+        }
+        RowTable t;
+        for (int j = 0; j < rows; ++j) {
+            t.src[j] = pk.src[j];
+            t.dst[j] = st.dst[j];
+        }
+        if (int rc = copy_crossing_rows(from, dst, t, sk, rows, plane_nodes(h->p), h->p.nx, h->elem, h->stream))
+            return rc;
+        return mem == LBM_MEM_HOST ? cuda_error(cudaStreamSynchronize(h->stream), "stream synchronize") : LBM_OK;
+    }
     if (mem == LBM_MEM_DEVICE) {
         RowTable t;
         for (int j = 0; j < rows; ++j) {

@@ -47,6 +47,20 @@ def _periodic2d():
     return f, dict(lattice=9, nx=70, ny=60, nz=1), 300
 
 
+def _box3d():
+    # walls on every axis, one x wall held at a temperature: at an x or y wall
+    # part of what a cut receives is the receiving node's own bounce-back
+    f = W.spinodal((36, 20, 26), rho0=0.9, T0=0.8, noise=2e-2, seed=43)
+    kw = dict(lattice=19, nx=26, ny=20, nz=36, wall=1, wall_x=1, wall_y=1, T_fixed_x=(1, 0), T_x=(0.84, 0.0),
+              T_fixed_lo=1, T_lo=0.86, gravity=(0.0, 0.0, -2e-5))
+    return f, kw, 120
+
+
+def _xwalls2d():
+    f = W.spinodal((1, 48, 50), rho0=1.0, T0=0.8, noise=1e-2, seed=44)
+    return f, dict(lattice=9, nx=50, ny=48, nz=1, wall_x=1, T_fixed_x=(0, 1), T_x=(0.0, 0.77)), 200
+
+
 def _run_whole(f, steps, **kw):
     sim = lbm.Lbm(**kw)
     try:
@@ -68,7 +82,7 @@ def _run_slabs(f, steps, count, **kw):
 
 
 @pytest.mark.parametrize("count", [1, 2, 3, 4])
-@pytest.mark.parametrize("case", [_walled3d, _periodic2d])
+@pytest.mark.parametrize("case", [_walled3d, _periodic2d, _box3d, _xwalls2d])
 def test_fp32_slabs_equal_the_undivided_domain_bit_for_bit(case, count):
     f, kw, steps = case()
     kw = dict(kw, storage=lbm.LBM_STORE_FP32)
@@ -92,6 +106,19 @@ def test_fp64_slabs_equal_the_undivided_domain_and_the_oracle(step_kernel):
     for k in KEYS:
         assert np.array_equal(whole[k], part[k]), k
     o = run_oracle(f, steps, **{k: v for k, v in kw.items() if k not in ("storage", "step_kernel")})
+    errs = {k: max_abs(part[k], o[k]) for k in KEYS}
+    assert all(v <= 1e-10 for v in errs.values()), errs
+
+
+def test_fp64_slabs_with_walls_across_the_cut_match_the_oracle():
+    f, kw, _ = _box3d()
+    steps = 40
+    kw = dict(kw, storage=lbm.LBM_STORE_FP64)
+    whole, _ = _run_whole(f, steps, **kw)
+    part, _ = _run_slabs(f, steps, 3, **kw)
+    for k in KEYS:
+        assert np.array_equal(whole[k], part[k]), k
+    o = run_oracle(f, steps, **{k: v for k, v in kw.items() if k != "storage"})
     errs = {k: max_abs(part[k], o[k]) for k in KEYS}
     assert all(v <= 1e-10 for v in errs.values()), errs
 
@@ -206,13 +233,70 @@ def test_crossing_copies_round_trip_and_reject_bad_arguments():
             b.close()
 
 
+def test_crossing_copies_leave_the_wall_columns_of_the_receiver_alone():
+    """With walls on x and y, lbm_set_crossing writes every node of a
+    crossing row except the wall column (row) of a direction whose velocity
+    points away from that wall, through a host buffer, an aligned device
+    buffer and a device buffer one value off a pair boundary (staged)."""
+    import torch
+    sys.path.insert(0, ROOT)
+    import oracle
+    f, kw, _ = _box3d()
+    nx, ny = kw["nx"], kw["ny"]
+    c = oracle.lattice(19)["c"]
+    for storage in (lbm.LBM_STORE_FP64, lbm.LBM_STORE_FP32, lbm.LBM_STORE_FP16):
+        esz = {0: 8, 1: 4, 2: 2}[storage]
+        a = lbm.Lbm(**dict(kw, storage=storage))
+        b = lbm.Lbm(**dict(kw, storage=storage))
+        try:
+            a.init(f.rho, np.ascontiguousarray(f.u), 1.5 * f.T)
+            b.init(np.full_like(f.rho, 0.5), np.zeros_like(f.u), np.full_like(f.T, 1.2))
+            a.step(3)
+            cb = lbm.lbm_crossing_bytes(a.h)
+            pb = lbm.lbm_plane_bytes(a.h)
+            for sign in (1, -1):
+                ks = np.flatnonzero(c[:, 2] == sign)
+                rows = np.empty(cb, dtype=np.uint8)
+                lbm.lbm_get_crossing(a.h, 11, sign, rows)
+                for how in ("host", "device", "unaligned"):
+                    before = np.empty(pb, dtype=np.uint8)
+                    lbm.lbm_get_planes(b.h, 7, 1, before)
+                    if how == "host":
+                        buf = rows
+                    else:
+                        off = 0 if how == "device" else esz
+                        big = torch.empty(cb + off, dtype=torch.uint8, device="cuda")
+                        big[off:] = torch.from_numpy(rows).cuda()
+                        buf = big[off:]
+                    lbm.lbm_set_crossing(b.h, 7, sign, buf)
+                    lbm.lbm_sync(b.h)
+                    after = np.empty(pb, dtype=np.uint8)
+                    lbm.lbm_get_planes(b.h, 7, 1, after)
+                    want = before.reshape(19, ny, nx, 2 * esz).copy()
+                    got_rows = rows.reshape(len(ks), ny, nx, 2 * esz)
+                    for j, k in enumerate(ks):
+                        keep = np.ones((ny, nx), dtype=bool)
+                        if c[k, 0]:
+                            keep[:, 0 if c[k, 0] > 0 else nx - 1] = False
+                        if c[k, 1]:
+                            keep[0 if c[k, 1] > 0 else ny - 1, :] = False
+                        want[k][keep] = got_rows[j][keep]
+                    assert np.array_equal(after, want.reshape(-1)), (storage, sign, how)
+                    # put b back for the next buffer kind
+                    lbm.lbm_set_planes(b.h, 7, 1, before)
+                    lbm.lbm_sync(b.h)
+        finally:
+            a.close()
+            b.close()
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         return s.getsockname()[1]
 
 
-def _slab_rank(rank, world, port, steps, out):
+def _slab_rank(rank, world, port, steps, out, case="walled"):
     sys.path.insert(0, ROOT)
     import torch
     import torch.distributed as dist
@@ -222,7 +306,7 @@ def _slab_rank(rank, world, port, steps, out):
     torch.cuda.set_device(0)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        f, kw, _ = _walled3d()
+        f, kw, _ = {"walled": _walled3d, "box": _box3d}[case]()
         r = SlabRank(dist, **dict(kw, storage=lbm.LBM_STORE_FP32))
         try:
             r.init(f.rho, f.u, 1.5 * f.T)
@@ -234,14 +318,15 @@ def _slab_rank(rank, world, port, steps, out):
         dist.destroy_process_group()
 
 
-def test_slab_ranks_in_two_processes_equal_the_undivided_domain():
+@pytest.mark.parametrize("case", ["walled", "box"])
+def test_slab_ranks_in_two_processes_equal_the_undivided_domain(case):
     world, steps = 2, 80
     ctx = mp.get_context("spawn")
     with ctx.Manager() as m:
         out = m.dict()
-        mp.spawn(_slab_rank, args=(world, _free_port(), steps, out), nprocs=world, join=True)
+        mp.spawn(_slab_rank, args=(world, _free_port(), steps, out, case), nprocs=world, join=True)
         got = dict(out)
-    f, kw, _ = _walled3d()
+    f, kw, _ = {"walled": _walled3d, "box": _box3d}[case]()
     whole, _ = _run_whole(f, steps, **dict(kw, storage=lbm.LBM_STORE_FP32))
     for r in range(world):
         first, own, m = got[r]

@@ -34,6 +34,13 @@ CASES = {
                                                    T_lo=0.85, chi_mode=1, chi=0.05)),
     # D3Q19 periodic in three slabs of 6, 6 and 5 planes: the first slab's lower halo wraps to the top
     "d3q19_periodic_3": dict(world=3, steps=10, p=dict(lattice=19, nx=6, ny=6, nz=17, latent=0.02)),
+    # D3Q19 closed box (walls on x, y and z, one x wall held at a temperature) in three slabs: at an x or y
+    # wall the populations a cut receives come partly from the receiving node's own bounce-back
+    "d3q19_box_3": dict(world=3, steps=10, p=dict(lattice=19, nx=7, ny=6, nz=15, wall=1, wall_x=1, wall_y=1,
+                                                 T_fixed_x=(1, 0), T_x=(0.84, 0.0), T_fixed_lo=1, T_lo=0.85)),
+    # D2Q9 walls on x, periodic last axis, two slabs
+    "d2q9_x_walls_2": dict(world=2, steps=30, p=dict(lattice=9, nx=18, ny=26, wall_x=1, T_fixed_x=(0, 1),
+                                                    T_x=(0.0, 0.76))),
 }
 
 
@@ -58,7 +65,11 @@ def _oracle_params(lp):
                          barotropic=bool(lp.barotropic), T0=lp.T0, tau=lp.tau, tau_E=lp.tau_E, c_v=lp.c_v,
                          chi_mode=bool(lp.chi_mode), lam=lp.lambda_, chi=lp.chi, g=tuple(lp.gravity),
                          wall=bool(lp.wall), T_fixed_lo=bool(lp.T_fixed_lo), T_fixed_hi=bool(lp.T_fixed_hi),
-                         T_lo=lp.T_lo, T_hi=lp.T_hi, pressure_work=bool(lp.pressure_work),
+                         T_lo=lp.T_lo, T_hi=lp.T_hi, wall_x=bool(lp.wall_x), wall_y=bool(lp.wall_y),
+                         T_fixed_x=(bool(lp.T_fixed_x[0]), bool(lp.T_fixed_x[1])),
+                         T_fixed_y=(bool(lp.T_fixed_y[0]), bool(lp.T_fixed_y[1])),
+                         T_x=(lp.T_x[0], lp.T_x[1]), T_y=(lp.T_y[0], lp.T_y[1]),
+                         pressure_work=bool(lp.pressure_work),
                          conduction=bool(lp.conduction), pseudoforce=bool(lp.pseudoforce), latent=lp.latent)
 
 
@@ -67,7 +78,8 @@ def _plane_view(a, Q, first, count):
     return a[:, first:first + count] if Q == 19 else a[:, :, first:first + count]
 
 
-def _rank(rank, world, port, case, out, leave_after, withhold_at=None, timeout_s=20, skip_round1=False):
+def _rank(rank, world, port, case, out, leave_after, withhold_at=None, timeout_s=20, skip_round1=False,
+          whole_rows=False):
     sys.path.insert(0, ROOT)
     import torch
     import torch.distributed as dist
@@ -100,8 +112,14 @@ def _rank(rank, world, port, case, out, leave_after, withhold_at=None, timeout_s
 
         # directions whose velocity component along the last axis is +1 / -1,
         # from the oracle's own velocity table
-        c_last = oracle.lattice(Q)["c"][:, 2 if Q == 19 else 1]
+        c = oracle.lattice(Q)["c"]
+        c_last = c[:, 2 if Q == 19 else 1]
         dirs = {sgn: np.flatnonzero(c_last == sgn) for sgn in (1, -1)}
+        # in-plane axes of a plane slice (Q, ny, nx) for D3Q19, (Q, nx) for D2Q9,
+        # with their walls: a crossing population that would come from beyond
+        # such a wall is not pushed by the neighbour; the receiving node's own
+        # bounce-back wrote it, so round 1 must leave it alone
+        walls = [(0, whole.wall_x, -1)] + ([(1, whole.wall_y, -2)] if Q == 19 else [])
 
         def get_cross(plane, sgn):
             k = dirs[sgn]
@@ -112,8 +130,20 @@ def _rank(rank, world, port, case, out, leave_after, withhold_at=None, timeout_s
             if skip_round1:
                 return
             a, k = t.numpy(), dirs[sgn]
-            _plane_view(st.N, Q, plane, 1)[k] = a[:len(k)]
-            _plane_view(st.g, Q, plane, 1)[k] = a[len(k):]
+            for f, vals in ((st.N, a[:len(k)]), (st.g, a[len(k):])):
+                pv = _plane_view(f, Q, plane, 1)          # (Q, 1, ny, nx) or (Q, 1, 1, nx)
+                shape = (len(k),) + ((pv.shape[2], pv.shape[3]) if Q == 19 else (pv.shape[3],))
+                cur, new = pv[k].reshape(shape), vals.reshape(shape)
+                keep = np.ones(shape, dtype=bool)
+                if not whole_rows:
+                    for j, kk in enumerate(k):
+                        for axis, walled, ax in walls:
+                            if walled and c[kk, axis] != 0:
+                                idx = [slice(None)] * (len(shape) - 1)
+                                idx[ax] = 0 if c[kk, axis] > 0 else -1
+                                keep[j][tuple(idx)] = False
+                cur[keep] = new[keep]
+                pv[k] = cur.reshape(pv[k].shape)
 
         for s in range(cfg["steps"]):
             if leave_after is not None and rank == world - 1 and s == leave_after:
@@ -214,3 +244,30 @@ def test_a_rank_that_withholds_its_halo_makes_the_swap_time_out():
     assert status == "failed" and step == at
     assert "Timed out" in msg or "timeout" in msg.lower()
     assert time.monotonic() - t0 < 60
+
+
+def test_whole_row_crossing_copies_break_walls_across_the_cut():
+    """Negative control for the wall rule of round 1: copying whole rows of
+    crossing populations overwrites what the receiving nodes' own
+    bounce-back at an x or y wall wrote, and the slabs no longer reproduce
+    the undivided oracle."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1705_10045_gb300 import lbm
+    case = "d3q19_box_3"
+    cfg = CASES[case]
+    world = cfg["world"]
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, _free_port(), case, out, None, None, 20, False, True), nprocs=world,
+                 join=True)
+        got = dict(out)
+    whole = lbm.make_params(**cfg["p"])
+    Q = whole.lattice
+    ref = oracle.State(_oracle_params(whole), *_fields(cfg["p"]))
+    ref.step(cfg["steps"])
+    diff = 0.0
+    for r in range(world):
+        first, own, n, e = got[r]
+        diff = max(diff, np.abs(n - _plane_view(ref.N, Q, first, own)).max())
+    assert diff > 1e-12

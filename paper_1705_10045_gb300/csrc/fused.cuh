@@ -265,17 +265,21 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
                                             R(V::w(k)) * p->E_ref, fN[k], fG[k]);
                 else
                     ld2(src, pair_index(k, nn, n), R(V::w(k)) * p->rho_ref, R(V::w(k)) * p->E_ref, fN[k], fG[k]);
-            R rho = 0, ja = 0, jb = 0, jm = 0, E = 0;
+            // opposite directions k, k+1 pair up: their sum enters rho, their
+            // difference the momentum along c_k (each sum starts at its
+            // first term)
+            R rho = fN[0], ja = R(0), jb = R(0), jm = R(0), E = fG[0];
+            bool new_a = true, new_b = true, new_m = true;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const R f = fN[k];
-                rho += f;
-                if (M::a(k) == 1) ja += f; else if (M::a(k) == -1) ja -= f;
-                if (M::b(k) == 1) jb += f; else if (M::b(k) == -1) jb -= f;
-                if (M::m(k) == 1) jm += f; else if (M::m(k) == -1) jm -= f;
+            for (int k = 1; k < Q; k += 2) {
+                const R s = fN[k] + fN[k + 1], d = fN[k] - fN[k + 1];
+                rho += s;
+                if (M::a(k) != 0) { const R t = M::a(k) > 0 ? d : -d; ja = new_a ? t : ja + t; new_a = false; }
+                if (M::b(k) != 0) { const R t = M::b(k) > 0 ? d : -d; jb = new_b ? t : jb + t; new_b = false; }
+                if (M::m(k) != 0) { const R t = M::m(k) > 0 ? d : -d; jm = new_m ? t : jm + t; new_m = false; }
             }
 #pragma unroll
-            for (int k = 0; k < Q; ++k) E += fG[k];
+            for (int k = 1; k < Q; ++k) E += fG[k];
             if constexpr (kSh) {   // sums of shifted values: sum_k w_k = 1, sum_k w_k c_k = 0
                 rho += p->rho_ref;
                 E += p->E_ref;
@@ -353,16 +357,29 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
         // finite differences below read shared memory.  The reload is the last
         // use of these lines on this SM, so it does not allocate them in L1.
         // The pointer walks from one direction's pair array to the next.
+        // With shifted FP16 storage the reload stays packed (one 32-bit word
+        // per pair, half the registers) and each half is widened where it is
+        // used.
         const int n = c * plane_n + n_ab;
         R fv[Q], hv[Q];
+        unsigned wv[Q];
         {
             const S* q = src + 2 * (size_t)n;
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
-                ld2_last(q, 0, R(V::w(k)) * p->rho_ref, R(V::w(k)) * p->E_ref, fv[k], hv[k]);
+                if constexpr (kSh) wv[k] = COH ? Store<S, R>::word_last_coh(q, 0) : Store<S, R>::word_last(q, 0);
+                else ld2_last(q, 0, R(V::w(k)) * p->rho_ref, R(V::w(k)) * p->E_ref, fv[k], hv[k]);
                 q += 2 * nn;
             }
         }
+        auto fvk = [&](int k) -> R {   // N_k (stored, shifted value with FP16)
+            if constexpr (kSh) return __half2float(__ushort_as_half((unsigned short)(wv[k] & 0xFFFFu)));
+            else return fv[k];
+        };
+        auto hvk = [&](int k) -> R {   // g_k
+            if constexpr (kSh) return __half2float(__ushort_as_half((unsigned short)(wv[k] >> 16)));
+            else return hv[k];
+        };
         const int sr = slotn(c, Sh::kRutSlots), sd = slotn(c, Sh::kDuSlots);
         const int fc = (tb + FB) * FW + ta + 1;        // 1-ring index of the node
         const R rho = rut(sr, 0, fc), T = rut(sr, 4, fc);
@@ -419,9 +436,9 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
         if (p->latent != R(0)) dE += latent_heat(*p, rho, T, div);
         if (fma(-rho, third, P) >= R(0)) atomicAdd(&cnt->clamps, 1ull);
 
-        R E = 0;
+        R E = hvk(0);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) E += hv[k];
+        for (int k = 1; k < Q; ++k) E += hvk(k);
         if constexpr (kSh) E += p->E_ref;
         if (!(finite_pos(rho) && finite_pos(E))) atomicAdd(&cnt->bad, 1ull);
         const R dEoverE = dE / E;
@@ -435,10 +452,18 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
         //   N*_k = (1 - omega) N_k + rho (omega e0_k + de_k)
         //   g*_k = (1 - omega_E + dE/E) g_k + E (omega_E e0_k + [pseudoforce] de_k)
         // with e0 = N^eq(rho,u)/rho and de = (N^eq(rho,u+du) - N^eq(rho,u))/rho.
-        // For opposite directions k, k+1 (c -> -c) both split into an even
-        // part (shared) and an odd part (sign flip).  Products that feed a sum
-        // are written as explicit fused multiply-adds, so every kernel that
-        // runs this code rounds them the same way.
+        // With v = u + du, s = c_k.u and t = c_k.v, Eq. (feq) gives
+        //   e0_k = w_k (b0 + 4.5 s^2 + 3 s),   de_k = w_k (db + 4.5 (t^2 - s^2) + 3 (t - s))
+        // (b0 = 1 - 1.5 u.u, db = -1.5 (v.v - u.u) = -1.5 du.(2u + du)), so
+        //   rho (omega e0_k + de_k) = w_k K + 4.5 w_k [P s^2 + rho t^2] + 3 w_k [P s + rho t]
+        // with K = rho omega b0 + rho db and P = rho omega - rho; the same holds
+        // for g with (E omega_E, E_pf) in place of (rho omega, rho).  Opposite
+        // directions k, k+1 (c -> -c) share the even part and flip the odd one.
+        // The factors w K, 4.5 w P, ... are formed once for the nearest
+        // directions and scaled by w2/w1 (1/2 on D3Q19, 1/4 on D2Q9: exact) for
+        // the next-nearest.  Products that feed a sum are written as explicit
+        // fused multiply-adds, so every kernel that runs this code rounds them
+        // the same way.
         const R usq = fma(u[0], u[0], fma(u[1], u[1], u[2] * u[2]));
         const R dsq = fma(dv[0], fma(R(2), u[0], dv[0]), fma(dv[1], fma(R(2), u[1], dv[1]), dv[2] * fma(R(2), u[2], dv[2])));
         const R base0 = fma(R(-1.5), usq, R(1)), dbase = R(-1.5) * dsq;
@@ -448,8 +473,12 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
         // shifted storage: with N_k = N'_k + w_k rho_ref and g_k = g'_k + w_k E_ref
         //   N*'_k = (1 - omega) N'_k + rho (omega e0_k + de_k) - omega w_k rho_ref
         //   g*'_k = fG g'_k + E (omega_E e0_k + [pf] de_k) + (fG - 1) w_k E_ref
-        // so the shifts enter as w_k nsh and w_k gsh in the source terms
+        // so the shifts enter K as nsh and gsh
         const R nsh = kSh ? -om * p->rho_ref : R(0), gsh = kSh ? (fG - R(1)) * p->E_ref : R(0);
+        const R KN = kSh ? fma(rho_om, base0, fma(rho, dbase, nsh)) : fma(rho_om, base0, rho * dbase);
+        const R KG = kSh ? fma(E_omE, base0, fma(E_pf, dbase, gsh)) : fma(E_omE, base0, E_pf * dbase);
+        const R PN = rho_om - rho, PG = E_omE - E_pf;
+        const R v[3] = {u[0] + dv[0], u[1] + dv[1], u[2] + dv[2]};
         const unsigned nbits = Store<S, R>::kStochastic ? node_bits(step, (unsigned)n) : 0u;
         S* dk = dst + 2 * (size_t)n;        // pair k of the node's slot (walks over k)
         // the collision and push, instantiated once for planes next to a wall
@@ -477,32 +506,35 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
                 else Store<S, R>::store2(dk + 2 * off, 0, fo, ho, wk * p->rho_ref, wk * p->E_ref, rN, rG);
                 dk += 2 * nn;
             };
-            {
-                const R w0 = R(V::w(0));
-                const R e0 = w0 * base0, de = w0 * dbase;
-                if constexpr (kSh)
-                    emit(0, fma(rho_om, e0, fma(rho, de, w0 * nsh)), fma(E_omE, e0, fma(E_pf, de, w0 * gsh)), fv[0],
-                         hv[0]);
-                else
-                    emit(0, fma(rho_om, e0, rho * de), fma(E_omE, e0, E_pf * de), fv[0], hv[0]);
-            }
+            emit(0, R(V::w(0)) * KN, R(V::w(0)) * KG, fvk(0), hvk(0));
+            constexpr double w1 = V::w(1);
+            R kn = R(w1) * KN, kg = R(w1) * KG;
+            R pn = R(4.5 * w1) * PN, qn = R(4.5 * w1) * rho, pg = R(4.5 * w1) * PG, qg = R(4.5 * w1) * E_pf;
+            R rn = R(3.0 * w1) * PN, sn = R(3.0 * w1) * rho, rg = R(3.0 * w1) * PG, sg = R(3.0 * w1) * E_pf;
 #pragma unroll
             for (int k = 1; k < Q; k += 2) {
-                const R wk = R(V::w(k));
-                R cu = 0, cd = 0;
-                if (M::a(k) == 1) { cu += u[0]; cd += dv[0]; } else if (M::a(k) == -1) { cu -= u[0]; cd -= dv[0]; }
-                if (M::b(k) == 1) { cu += u[1]; cd += dv[1]; } else if (M::b(k) == -1) { cu -= u[1]; cd -= dv[1]; }
-                if (M::m(k) == 1) { cu += u[2]; cd += dv[2]; } else if (M::m(k) == -1) { cu -= u[2]; cd -= dv[2]; }
-                const R ev = wk * fma(R(4.5) * cu, cu, base0), od = (R(3) * wk) * cu;
-                const R dv_e = wk * fma(R(4.5) * cd, fma(R(2), cu, cd), dbase), dv_o = (R(3) * wk) * cd;
-                // direction k takes e0 = ev + od, de = dv_e + dv_o and k + 1
-                // the differences: the even and odd parts of the sources are
-                // formed once for both
-                const R aE = kSh ? fma(rho_om, ev, fma(rho, dv_e, wk * nsh)) : fma(rho_om, ev, rho * dv_e);
-                const R bE = kSh ? fma(E_omE, ev, fma(E_pf, dv_e, wk * gsh)) : fma(E_omE, ev, E_pf * dv_e);
-                const R aO = fma(rho_om, od, rho * dv_o), bO = fma(E_omE, od, E_pf * dv_o);
-                emit(k, aE + aO, bE + bO, fv[k], hv[k]);
-                emit(k + 1, aE - aO, bE - bO, fv[k + 1], hv[k + 1]);
+                if (k == (Q == 19 ? 7 : 5)) {   // first next-nearest direction
+                    const R h = R(V::w(Q - 1) / w1);
+                    kn *= h; kg *= h; pn *= h; qn *= h; pg *= h; qg *= h; rn *= h; sn *= h; rg *= h; sg *= h;
+                }
+                // s = c_k.u and t = c_k.v, each summed from its first term
+                R s = R(0), t = R(0);
+                bool first = true;
+                auto add = [&](int cc, R x, R y) {
+                    if (cc == 0) return;
+                    const R xs = cc > 0 ? x : -x, ys = cc > 0 ? y : -y;
+                    s = first ? xs : s + xs;
+                    t = first ? ys : t + ys;
+                    first = false;
+                };
+                add(M::a(k), u[0], v[0]);
+                add(M::b(k), u[1], v[1]);
+                add(M::m(k), u[2], v[2]);
+                const R s2 = s * s, t2 = t * t;
+                const R aE = fma(pn, s2, fma(qn, t2, kn)), bE = fma(pg, s2, fma(qg, t2, kg));
+                const R aO = fma(rn, s, sn * t), bO = fma(rg, s, sg * t);
+                emit(k, aE + aO, bE + bO, fvk(k), hvk(k));
+                emit(k + 1, aE - aO, bE - bO, fvk(k + 1), hvk(k + 1));
             }
         };
         if (wall_lo || wall_hi || edge) collide(std::true_type{});

@@ -499,11 +499,10 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
                 if (M::m(k) == 1) to += dM_p; else if (M::m(k) == -1) to += dM_m;
                 // opposite directions share a weight, so the FP16 shift of slot ko is w_k ref
                 const R wk = R(V::w(k));
-                unsigned rN = 0, rG = 0;
-                if (Store<S, R>::kStochastic) pair_bits(nbits, k, rN, rG);
+                const unsigned t = Store<S, R>::kStochastic ? pair_word(nbits, k) : 0u;
                 const long long off = bounce ? (long long)(opposite(k) - k) * (long long)nn : (long long)to;
-                if constexpr (kSh) Store<S, R>::store2_raw(dk + 2 * off, 0, fo, ho, rN, rG);
-                else Store<S, R>::store2(dk + 2 * off, 0, fo, ho, wk * p->rho_ref, wk * p->E_ref, rN, rG);
+                if constexpr (kSh) Store<S, R>::store2_raw(dk + 2 * off, 0, fo, ho, t);
+                else Store<S, R>::store2(dk + 2 * off, 0, fo, ho, wk * p->rho_ref, wk * p->E_ref, t);
                 dk += 2 * nn;
             };
             emit(0, R(V::w(0)) * KN, R(V::w(0)) * KG, fvk(0), hvk(0));

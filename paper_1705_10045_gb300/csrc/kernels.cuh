@@ -216,10 +216,8 @@ __global__ void __launch_bounds__(256) collide_kernel(const S* __restrict__ src,
         Nb m = neighbour<D>(x, y, z, V::cx(k), V::cy(k), V::cz(k), p);
         const int ko = m.ghost ? opposite(k) : k;
         const long long to = m.ghost ? i : m.n;
-        unsigned rN, rG;
-        pair_bits(nbits, k, rN, rG);
         Store<S, R>::store2(dst, pair_index(ko, nn, to), fs, hs, R(V::w(ko)) * p.rho_ref, R(V::w(ko)) * p.E_ref,
-                            rN, rG);
+                            pair_word(nbits, k));
     }
 }
 
@@ -257,9 +255,8 @@ __global__ void __launch_bounds__(256) init_kernel(S* __restrict__ pop, const do
         const R wk = R(V::w(k));
         const R cu = cdot<Q, R>(k, u[0], u[1], u[2]);
         const R e0 = wk * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
-        unsigned rN, rG;
-        pair_bits(nbits, k, rN, rG);
-        Store<S, R>::store2(pop, pair_index(k, nn, i), rho * e0, E * e0, wk * p.rho_ref, wk * p.E_ref, rN, rG);
+        Store<S, R>::store2(pop, pair_index(k, nn, i), rho * e0, E * e0, wk * p.rho_ref, wk * p.E_ref,
+                            pair_word(nbits, k));
     }
 }
 

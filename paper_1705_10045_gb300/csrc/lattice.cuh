@@ -68,9 +68,11 @@ __host__ __device__ constexpr int opposite(int k) { return k == 0 ? 0 : ((k & 1)
 // f - w_k * ref (ref = rho_ref for N, E_ref for g) with stochastic rounding:
 // a node that keeps nearly the same populations step after step would
 // otherwise round the same way every step, and round-to-nearest then drifts
-// the mass and energy linearly in time.  The 13 random bits added below the
-// FP16 mantissa come from a counter-based hash of (step, node, slot), so a
-// run is reproducible bit for bit and resumes exactly from a checkpoint.
+// the mass and energy linearly in time.  The rounding is the hardware's
+// stochastic-rounding conversion (cvt.rs), which rounds a value up with
+// probability equal to the fraction it discards; its random bits come from a
+// counter-based hash of (step, node, direction), so a run is reproducible
+// bit for bit and resumes exactly from a checkpoint.
 
 // "lowbias32" integer hash (C. Wellons' published 32-bit mixer)
 __host__ __device__ __forceinline__ unsigned mix32(unsigned x) {
@@ -82,16 +84,13 @@ __host__ __device__ __forceinline__ unsigned mix32(unsigned x) {
     return x;
 }
 
-// per-node random word of one step; the 13 bits of the pair of direction k
-// come from one product t = node_bits * (2k + 1) * golden ratio constant: its
-// top 13 bits for N_k and bits 6..18 for g_k
+// per-node random word of one step, and the word of the pair of direction k:
+// one product nb * (2k + 1) * golden ratio constant
 __device__ __forceinline__ unsigned node_bits(unsigned step, unsigned n) {
     return mix32(n * 0x9E3779B1u ^ mix32(step + 0x632BE5ABu));
 }
-__device__ __forceinline__ void pair_bits(unsigned nb, int k, unsigned& rN, unsigned& rG) {
-    const unsigned t = nb * ((2u * (unsigned)k + 1u) * 0x9E3779B9u);
-    rN = t >> 19;
-    rG = (t >> 6) & 0x1FFFu;
+__device__ __forceinline__ unsigned pair_word(unsigned nb, int k) {
+    return nb * ((2u * (unsigned)k + 1u) * 0x9E3779B9u);
 }
 
 // Population layout in device memory.  Every kernel reads a node's N_k and
@@ -110,7 +109,7 @@ __host__ __device__ __forceinline__ size_t pair_index(int k, long long nn, long 
 template <typename S, typename R> struct Store;
 // load: one value at element index i (the set-major checkpoint layout).
 // load2 / store2: the pair (N_k, g_k) at pair index i in one access (shifts
-// sN, sG; random bits rN, rG of the FP16 rounding).  load2_keep: a first read
+// sN, sG; random word t of the FP16 rounding).  load2_keep: a first read
 // of lines the same SM reads again soon (L2 evict-last where it pays).
 // load2_last: the read of a value's last use on this SM (the fused step's
 // consumer reload); L1::no_allocate leaves L1 to the lines the moment stage
@@ -139,8 +138,7 @@ template <> struct Store<double, double> {
         asm volatile("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p + 2 * i)
                      : "memory");
     }
-    __device__ static void store2(double* p, size_t i, double a, double b, double, double, unsigned = 0,
-                                  unsigned = 0) {
+    __device__ static void store2(double* p, size_t i, double a, double b, double, double, unsigned = 0) {
         reinterpret_cast<double2*>(p)[i] = make_double2(a, b);
     }
 };
@@ -171,7 +169,7 @@ template <> struct Store<float, float> {
     // the stored pair is read again only in the next step, after the whole
     // domain has streamed through L2: evict-first keeps L2 for the lines the
     // step itself still reads
-    __device__ static void store2(float* p, size_t i, float a, float b, float, float, unsigned = 0, unsigned = 0) {
+    __device__ static void store2(float* p, size_t i, float a, float b, float, float, unsigned = 0) {
         unsigned long long pol;
         asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
         asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p + 2 * i), "f"(a), "f"(b), "l"(pol)
@@ -240,18 +238,15 @@ template <> struct Store<__half, float> {
     __device__ static void load2_last_coh_raw(const __half* p, size_t i, float& a, float& b) {
         unpack_raw(word_last_coh(p, i), a, b);
     }
-    // both halves rounded toward zero by one packed conversion (g_k high);
-    // a, b already shifted
-    __device__ static void store2_raw(__half* p, size_t i, float a, float b, unsigned rN, unsigned rG) {
-        const float ra = __uint_as_float(__float_as_uint(a) + (rN & 0x1FFFu));
-        const float rb = __uint_as_float(__float_as_uint(b) + (rG & 0x1FFFu));
+    // both halves rounded stochastically by one packed conversion (g_k in the
+    // high half) with the random word t; a, b already shifted
+    __device__ static void store2_raw(__half* p, size_t i, float a, float b, unsigned t) {
         unsigned w;
-        asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(rb), "f"(ra));
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(b), "f"(a), "r"(t));
         reinterpret_cast<unsigned*>(p)[i] = w;
     }
-    __device__ static void store2(__half* p, size_t i, float a, float b, float sN, float sG, unsigned rN = 0,
-                                  unsigned rG = 0) {
-        store2_raw(p, i, a - sN, b - sG, rN, rG);
+    __device__ static void store2(__half* p, size_t i, float a, float b, float sN, float sG, unsigned t = 0) {
+        store2_raw(p, i, a - sN, b - sG, t);
     }
 };
 

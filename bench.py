@@ -12,10 +12,11 @@ energy change, collision of both population sets, streaming, walls).
 Prints one JSON line (rank 0).  With one GPU the workload runs undivided.
 With N > 1 ranks (torchrun, one GPU each) the default mode cuts the one
 domain into N slabs along z, one per rank, each holding two halo planes beyond
-each cut; after every step a rank sends the populations its edge planes pushed
-across a cut to the neighbour that owns them, then refreshes its halo planes
-from the neighbours' edge planes, over NCCL point to point (strong scaling:
-value = the domain's lattice updates per second); --mode replicas
+each cut; every step a rank steps the planes next to its cuts, sends each
+neighbour the populations it pushed across the cut and its two edge planes
+over NCCL point to point while its interior steps, and then refreshes its
+halo planes (strong scaling: value = the domain's lattice updates per
+second); --mode replicas
 runs an independent copy per rank instead (weak scaling).  The populations
 (11.5 GB of reads and writes per step) are far larger than L2, so no flush is
 needed.
@@ -491,10 +492,11 @@ def serving_bench(count: int = 128, storage: int = None, seed: int = 5, rate: fl
 
 def slab_main(args, ws, rank, dist):
     """One domain cut into `ws` z-slabs, slab r on rank r (slabs.SlabRank over
-    NCCL): every step launches the slab's fused step over its owned planes,
-    then swaps the crossing populations and the two halo planes with each
-    neighbour.  Timed like the undivided run; value is the whole domain's
-    MLUPS (strong scaling)."""
+    NCCL): every step launches the slab's fused step over the planes next to
+    its cuts, posts the swap (crossing populations and two edge planes to each
+    neighbour), steps its interior planes while the messages travel, and then
+    applies what it received.  Timed like the undivided run; value is the
+    whole domain's MLUPS (strong scaling)."""
     import torch
     from paper_1705_10045_gb300 import lbm
     from paper_1705_10045_gb300 import slabs as SL
@@ -554,9 +556,11 @@ def slab_main(args, ws, rank, dist):
             "e2e": {"value": nn * args.steps / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps},
             "halo_bytes_per_rank_per_step": halo_bytes * 2,
-            # per step: the fused step, and per neighbour four copy kernels
-            # (crossing populations out and in, edge planes out, halo planes in)
-            "gpu_launches": args.steps * (1 + 4 * sides),
+            # per step: the fused step in ranges (planes next to the cuts, then
+            # the interior), and per neighbour five copy kernels (crossing
+            # populations and edge planes out; halo planes, own crossing
+            # populations and the neighbour's in)
+            "gpu_launches": args.steps * (sum(len(x) for x in r._ranges()) + 5 * sides),
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

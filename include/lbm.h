@@ -397,6 +397,27 @@ int lbm_set_planes(lbm_handle* h, int first, int count, const void* buf, int mem
  * handle, range outside the last axis. */
 int lbm_set_step_planes(lbm_handle* h, int first, int count);
 
+/* One step of the fused form in pieces, so that a slab can step the planes
+ * next to its cuts first and swap them with its neighbours while its interior
+ * steps (the step of Sec. 2-4 is the same per node whatever the order in
+ * which planes are collided: every plane reads the step's input and writes
+ * its own pushes).  lbm_step_begin collides planes [first, first + count) of
+ * the last axis, asynchronously on the handle's stream.  The first call of a
+ * step opens it: from then on the step's output is the handle's current
+ * state, so lbm_get_planes / lbm_set_planes / lbm_get_crossing /
+ * lbm_set_crossing act on planes the launches so far have written, and the
+ * step count (the FP16 rounding seed) has advanced.  Later calls add ranges to
+ * the same step; the ranges of one step must not overlap.  lbm_step_end
+ * closes the step.  A range stepped this way writes exactly what lbm_step
+ * writes for those planes, so ranges that cover [0, nm) (or the range of
+ * lbm_set_step_planes) reproduce lbm_step bit for bit.  While a step is open,
+ * lbm_step, lbm_profile_step, lbm_init and lbm_set_state refuse
+ * (LBM_ERR_INVALID_ARG).  Errors (LBM_ERR_INVALID_ARG): null handle, no state
+ * yet, a range outside the last axis, the three-launch step form; lbm_step_end
+ * with no open step. */
+int lbm_step_begin(lbm_handle* h, int first, int count);
+int lbm_step_end(lbm_handle* h);
+
 /* The populations that cross a cut of the last axis, for the first exchange
  * round between processes: bytes of one plane's pairs (N_k, g_k) for the
  * directions whose velocity component along the last axis is +1 (the same
@@ -412,7 +433,8 @@ size_t lbm_crossing_bytes(const lbm_handle* h);
  * pushes those populations across the cut (they would come from beyond the
  * wall); the receiving node's own bounce-back wrote them in its step.  With
  * such walls and a host buffer, or a device buffer not aligned to a pair, it
- * stages the rows in the handle's idle population buffer.  Errors
+ * stages the rows in the handle's host-transfer buffer (allocated on first
+ * use, as by lbm_moments with host pointers).  Errors
  * (LBM_ERR_INVALID_ARG): null pointers, bad mem flag, sign not +1 / -1, no
  * state yet, plane outside the last axis. */
 int lbm_get_crossing(lbm_handle* h, int plane, int sign, void* buf, int mem);

@@ -71,14 +71,20 @@ template <int Q, typename S, typename R> struct Impl {
     static constexpr bool SPLIT = FusedTile<Q, R>::SPLIT;
     static int launches(const lbm_handle* h) { return h->p.step_kernel == LBM_STEP_THREE_LAUNCH ? 3 : 1; }
 
-    static MarchGeom geometry(const lbm_handle* h) {
+    // planes [m_lo, m_hi) collided; m_hi < 0: the handle's own range
+    // (lbm_set_step_planes; all by default)
+    static MarchGeom geometry(const lbm_handle* h, int m_lo = 0, int m_hi = -1) {
         MarchGeom G;
         G.na = h->p.nx;
         G.nb = Q == 9 ? 1 : h->p.ny;
         G.nm = Q == 9 ? h->p.ny : h->p.nz;
-        // planes collided (lbm_set_step_planes; all by default)
-        G.m_lo = h->step_count > 0 ? h->step_first : 0;
-        G.m_hi = h->step_count > 0 ? h->step_first + h->step_count : G.nm;
+        if (m_hi < 0) {
+            G.m_lo = h->step_count > 0 ? h->step_first : 0;
+            G.m_hi = h->step_count > 0 ? h->step_first + h->step_count : G.nm;
+        } else {
+            G.m_lo = m_lo;
+            G.m_hi = m_hi;
+        }
         const int len = G.m_hi - G.m_lo;
         // planes per CTA: enough CTAs for about two per SM on 152 SMs, and
         // at least 8 planes so that the extra ring planes stay a minority
@@ -90,7 +96,12 @@ template <int Q, typename S, typename R> struct Impl {
     }
 
     static void launch_fused(lbm_handle* h, const KParams<R>& kp) {
-        const MarchGeom G = geometry(h);
+        launch_fused_range(h, kp, geometry(h), (const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1]);
+        h->cur ^= 1;
+    }
+
+    // the fused step over the planes of G, src -> dst (no buffer swap)
+    static void launch_fused_range(lbm_handle* h, const KParams<R>& kp, const MarchGeom& G, const S* src, S* dst) {
         const size_t smem = FusedShape<TX, TY, SPLIT>::template smem_bytes<R>();
         const bool xw = h->p.wall_x || (Q == 19 && h->p.wall_y);
         auto kern = xw ? fused_step_kernel<Q, S, R, TX, TY, NP, true, SPLIT>
@@ -103,13 +114,20 @@ template <int Q, typename S, typename R> struct Impl {
         if (h->fault_drop > 0) {   // fault-injection test hook (lbm_test_drop_handoff)
             auto fk = fused_step_fault_kernel<Q, S, R, TX, TY, NP, SPLIT>;
             cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            fk<<<grid, TX * TY + NP, smem, h->stream>>>((const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], kp, G,
-                                                        (Counters*)h->cnt, h->fault_drop - 1);
+            fk<<<grid, TX * TY + NP, smem, h->stream>>>(src, dst, kp, G, (Counters*)h->cnt, h->fault_drop - 1);
         } else {
-            kern<<<grid, TX * TY + NP, smem, h->stream>>>((const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], kp, G,
-                                                     (Counters*)h->cnt);
+            kern<<<grid, TX * TY + NP, smem, h->stream>>>(src, dst, kp, G, (Counters*)h->cnt);
         }
-        h->cur ^= 1;
+    }
+
+    // planes [first, first + count) of the step lbm_step_begin opened: it has
+    // already made the destination buffer current, so the source is the other
+    static int step_range(lbm_handle* h, int first, int count) {
+        KParams<R> kp = make_kparams<R>(h);
+        kp.step = (unsigned)h->pending_step;
+        launch_fused_range(h, kp, geometry(h, first, first + count), (const S*)h->pop[h->cur ^ 1],
+                           (S*)h->pop[h->cur]);
+        return cuda_error(cudaGetLastError(), "lbm_step_begin launch");
     }
 
     // launch j of one time step; the last launch of a step swaps the buffers
@@ -340,6 +358,9 @@ template <int Q, typename S, typename R> int Impl<Q, S, R>::batch_launch(lbm_bat
     }
 
 template <int Q> int Backend<Q>::step(lbm_handle* h, int n) { LBM_DISPATCH(h, step(h, n)); }
+template <int Q> int Backend<Q>::step_range(lbm_handle* h, int first, int count) {
+    LBM_DISPATCH(h, step_range(h, first, count));
+}
 template <int Q> int Backend<Q>::profile(lbm_handle* h, int n, double* ms, int cap) {
     LBM_DISPATCH(h, profile(h, n, ms, cap));
 }

@@ -27,6 +27,8 @@ struct lbm_handle {
     int fault_drop = 0;         // lbm_test_drop_handoff hook: 1 + plane, 0 = off
     int step_first = 0;         // lbm_set_step_planes: the fused step collides planes
     int step_count = 0;         // [step_first, step_first + step_count) of the last axis (0: all)
+    bool pending = false;       // lbm_step_begin opened a step that lbm_step_end has not closed
+    long long pending_step = 0; // its step count (the FP16 rounding seed)
     cudaStream_t stream = nullptr;
 };
 
@@ -75,11 +77,13 @@ struct TraceRange {
 // error reporting shared by the translation units
 void set_error(const std::string& msg);
 int cuda_error(cudaError_t e, const char* where);
+int ensure_staging(lbm_handle* h);   // the handle's host-transfer buffer, allocated on first use
 
 
 // per-lattice entry points, dispatched on the storage format inside
 template <int Q> struct Backend {
     static int step(lbm_handle* h, int n);
+    static int step_range(lbm_handle* h, int first, int count);   // planes of the step lbm_step_begin opened
     static int profile(lbm_handle* h, int n, double* ms, int cap);   // returns launches per step
     static const char* launch_name(const lbm_handle* h, int j);
     static int launches(const lbm_handle* h);

@@ -84,13 +84,21 @@ __host__ __device__ __forceinline__ unsigned mix32(unsigned x) {
     return x;
 }
 
-// per-node random word of one step, and the word of the pair of direction k:
-// one product nb * (2k + 1) * golden ratio constant
+// per-node random word of one step, and the word of the pair of direction k.
+// The conversion rounds the low half of a pair with bits 0..12 of the word
+// and the high half with bits 16..28.  t = nb * (2k + 1) * golden ratio
+// constant (mod 2^32) is uniform, since multiplying by an odd constant is a
+// bijection; but its bits 0..12 depend on those of nb alone, the same few
+// bits for every direction of a node.  The word is therefore t ^ (t >> 16):
+// its low field mixes in bits 16..28, which depend on nearly all of nb, and
+// both fields stay uniform and independent of each other.  (The high half of
+// a 64-bit product is not uniform, and rounding with it drifted the energy.)
 __device__ __forceinline__ unsigned node_bits(unsigned step, unsigned n) {
     return mix32(n * 0x9E3779B1u ^ mix32(step + 0x632BE5ABu));
 }
 __device__ __forceinline__ unsigned pair_word(unsigned nb, int k) {
-    return nb * ((2u * (unsigned)k + 1u) * 0x9E3779B9u);
+    const unsigned t = nb * ((2u * (unsigned)k + 1u) * 0x9E3779B9u);
+    return t ^ (t >> 16);
 }
 
 // Population layout in device memory.  Every kernel reads a node's N_k and

@@ -30,9 +30,18 @@ int cuda_error(cudaError_t e, const char* where) {
     return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
 }
 
+// the handle's (D + 3)-plane device buffer for host transfers, allocated on
+// first use
+int ensure_staging(lbm_handle* h) {
+    if (h->staging) return LBM_OK;
+    return cuda_error(cudaMalloc((void**)&h->staging, sizeof(double) * (size_t)(h->D + 3) * h->nn),
+                      "staging allocation");
+}
+
 }  // namespace lbm
 
 using lbm::cuda_error;
+using lbm::ensure_staging;
 using lbm::set_error;
 
 namespace {
@@ -100,6 +109,16 @@ int need_init(const lbm_handle* h) {
     return LBM_OK;
 }
 
+// calls that start a step or replace the state wait for an open split step
+// (lbm_step_begin) to be closed
+int no_pending(const lbm_handle* h, const char* who) {
+    if (h->pending) {
+        set_error(std::string(who) + ": a step opened by lbm_step_begin is still open (call lbm_step_end)");
+        return LBM_ERR_INVALID_ARG;
+    }
+    return LBM_OK;
+}
+
 // Coexistence table of the latent-heat source in the kernels' arithmetic
 // type: rho_v at the kCoexIntervals + 1 grid temperatures, then rho_l.
 int upload_coexistence(lbm_handle* h) {
@@ -112,12 +131,6 @@ int upload_coexistence(lbm_handle* h) {
     if (dbl) return cuda_error(cudaMemcpy(h->coex, tab.data(), bytes, cudaMemcpyHostToDevice), "coexistence table");
     std::vector<float> f(tab.begin(), tab.end());
     return cuda_error(cudaMemcpy(h->coex, f.data(), bytes, cudaMemcpyHostToDevice), "coexistence table");
-}
-
-int ensure_staging(lbm_handle* h) {
-    if (h->staging) return LBM_OK;
-    return cuda_error(cudaMalloc((void**)&h->staging, sizeof(double) * (size_t)(h->D + 3) * h->nn),
-                      "staging allocation");
 }
 
 int be_step(lbm_handle* h, int n) {
@@ -283,6 +296,7 @@ int lbm_coexistence(double T, double* rho_v, double* rho_l) {
 int lbm_init(lbm_handle* h, const double* rho, const double* u, const double* eps, int mem) {
     lbm::TraceRange trace_("lbm_init");
     if (int rc = check_handle(h)) return rc;
+    if (int rc = no_pending(h, "lbm_init")) return rc;
     if (!rho || !u || !eps || (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE)) {
         set_error("lbm_init: null field or bad mem flag");
         return LBM_ERR_INVALID_ARG;
@@ -332,6 +346,7 @@ int lbm_step(lbm_handle* h, int n) {
     lbm::TraceRange trace_("lbm_step");
     if (int rc = check_handle(h)) return rc;
     if (int rc = need_init(h)) return rc;
+    if (int rc = no_pending(h, "lbm_step")) return rc;
     if (n < 0) {
         set_error("lbm_step: n < 0");
         return LBM_ERR_INVALID_ARG;
@@ -341,6 +356,39 @@ int lbm_step(lbm_handle* h, int n) {
     int rc = be_step(h, n);
     if (!rc) h->steps += n;
     return rc;
+}
+
+int lbm_step_begin(lbm_handle* h, int first, int count) {
+    lbm::TraceRange trace_("lbm_step_begin");
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = need_init(h)) return rc;
+    const int nm = h->Q == 9 ? h->p.ny : h->p.nz;
+    if (first < 0 || count < 1 || first + count > nm) {
+        set_error("lbm_step_begin: planes [first, first + count) outside [0, " + std::to_string(nm) + ")");
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (h->p.step_kernel == LBM_STEP_THREE_LAUNCH) {
+        set_error("lbm_step_begin: split steps need the fused step kernel");
+        return LBM_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(h->p.device);
+    if (!h->pending) {   // open the step: its destination becomes the current state
+        h->pending = true;
+        h->pending_step = h->steps;
+        h->cur ^= 1;
+        h->steps += 1;
+    }
+    return h->Q == 9 ? lbm::Backend<9>::step_range(h, first, count) : lbm::Backend<19>::step_range(h, first, count);
+}
+
+int lbm_step_end(lbm_handle* h) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h->pending) {
+        set_error("lbm_step_end: no step is open");
+        return LBM_ERR_INVALID_ARG;
+    }
+    h->pending = false;
+    return LBM_OK;
 }
 
 int lbm_moments(lbm_handle* h, double* rho, double* u, double* T, double* P, int mem) {
@@ -481,6 +529,7 @@ int lbm_get_state(lbm_handle* h, void* buf, int mem) {
 int lbm_set_state(lbm_handle* h, const void* buf, int mem) {
     lbm::TraceRange trace_("lbm_set_state");
     if (int rc = check_handle(h)) return rc;
+    if (int rc = no_pending(h, "lbm_set_state")) return rc;
     if (!buf || (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE)) {
         set_error("lbm_set_state: null buffer or bad mem flag");
         return LBM_ERR_INVALID_ARG;
@@ -535,6 +584,7 @@ int lbm_profile_step(lbm_handle* h, int n, double* ms, int cap) {
     lbm::TraceRange trace_("lbm_profile_step");
     if (int rc = check_handle(h)) return rc;
     if (int rc = need_init(h)) return rc;
+    if (int rc = no_pending(h, "lbm_profile_step")) return rc;
     if (n < 1 || !ms || cap < 1) {
         set_error("lbm_profile_step: need n >= 1 and an output array");
         return LBM_ERR_INVALID_ARG;

@@ -335,8 +335,8 @@ int check_slabs(const lbm_slabs* s) {
     return LBM_OK;
 }
 
-// the two rounds of the exchange (see the top of this file), on the caller's stream
-int exchange(lbm_slabs* s) {
+// the two rounds of the exchange (see the top of this file), on `stream`
+int exchange(lbm_slabs* s, cudaStream_t stream) {
     const int H = LBM_SLAB_HALO;
     // (1) crossing populations: slab i's upper edge plane pushed them into its
     // halo plane lo + own, its lower edge plane into lo - 1
@@ -344,11 +344,11 @@ int exchange(lbm_slabs* s) {
         const lbm_slab& a = s->plan[i];
         if (a.hi) {
             const lbm_slab& b = s->plan[a.above];
-            if (int rc = copy_crossing(s->h[a.above], b.lo, s->h[i], a.lo + a.own, +1, s->main)) return rc;
+            if (int rc = copy_crossing(s->h[a.above], b.lo, s->h[i], a.lo + a.own, +1, stream)) return rc;
         }
         if (a.lo) {
             const lbm_slab& b = s->plan[a.below];
-            if (int rc = copy_crossing(s->h[a.below], b.lo + b.own - 1, s->h[i], a.lo - 1, -1, s->main))
+            if (int rc = copy_crossing(s->h[a.below], b.lo + b.own - 1, s->h[i], a.lo - 1, -1, stream))
                 return rc;
         }
     }
@@ -357,11 +357,11 @@ int exchange(lbm_slabs* s) {
         const lbm_slab& a = s->plan[i];
         if (a.hi) {
             const lbm_slab& b = s->plan[a.above];
-            if (int rc = copy_planes(s->h[i], a.lo + a.own, s->h[a.above], b.lo, H, s->main)) return rc;
+            if (int rc = copy_planes(s->h[i], a.lo + a.own, s->h[a.above], b.lo, H, stream)) return rc;
         }
         if (a.lo) {
             const lbm_slab& b = s->plan[a.below];
-            if (int rc = copy_planes(s->h[i], 0, s->h[a.below], b.lo + b.own - H, H, s->main)) return rc;
+            if (int rc = copy_planes(s->h[i], 0, s->h[a.below], b.lo + b.own - H, H, stream)) return rc;
         }
     }
     return LBM_OK;
@@ -526,8 +526,10 @@ int lbm_slabs_step(lbm_slabs* s, int n) {
     for (int t = 0; t < n; ++t) {
         for (int i = 0; i < s->count; ++i)
             if (int rc = lbm_step(s->h[i], 1)) return rc;
-        lbm::TraceRange swap_("halo swap");
-        if (int rc = exchange(s)) return rc;
+        if (s->count > 1) {
+            lbm::TraceRange swap_("halo swap");
+            if (int rc = exchange(s, s->main)) return rc;
+        }
         ++s->steps;
     }
     return LBM_OK;
@@ -769,11 +771,19 @@ int lbm_set_crossing(lbm_handle* h, int plane, int sign, const void* buf, int me
     if (crossing_skips(h->p, ks, rows, sk)) {
         // walls across the plane: the rows go through the wall-skipping copy,
         // from the caller's device buffer if it is aligned to a pair, else
-        // staged in the idle population buffer (free between steps)
+        // staged in the handle's host-transfer buffer ((D + 3) planes of
+        // doubles: room for the crossing rows of a plane of any slab of at
+        // least two planes; no step reads it)
         const long long e = 2 * (long long)h->elem;
         const void* from = buf;
         if (mem == LBM_MEM_HOST || ((unsigned long long)(size_t)buf % (unsigned long long)e) != 0) {
-            auto* stage = static_cast<unsigned char*>(h->pop[h->cur ^ 1]);
+            if ((size_t)(rows * width) > sizeof(double) * (size_t)(h->D + 3) * (size_t)h->nn) {
+                set_error("lbm_set_crossing: a domain of one plane cannot stage the crossing rows; pass an aligned "
+                          "device buffer");
+                return LBM_ERR_INVALID_ARG;
+            }
+            if (int rc = lbm::ensure_staging(h)) return rc;
+            auto* stage = reinterpret_cast<unsigned char*>(h->staging);
             const cudaMemcpyKind kind = mem == LBM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
             if (int rc = cuda_error(cudaMemcpyAsync(stage, buf, (size_t)(rows * width), kind, h->stream),
                                     "crossing copy"))

@@ -47,7 +47,7 @@ EXPORTED = ("lbm_default_params", "lbm_create", "lbm_init", "lbm_step", "lbm_mom
             "lbm_slabs_create", "lbm_slabs_count", "lbm_slabs_domain", "lbm_slabs_init", "lbm_slabs_step",
             "lbm_slabs_moments", "lbm_slabs_diagnostics", "lbm_slabs_sync", "lbm_slabs_destroy", "lbm_plane_bytes",
             "lbm_get_planes", "lbm_set_planes", "lbm_moments_f", "lbm_set_step_planes", "lbm_crossing_bytes",
-            "lbm_get_crossing", "lbm_set_crossing")
+            "lbm_get_crossing", "lbm_set_crossing", "lbm_step_begin", "lbm_step_end")
 LBM_SLAB_HALO = 2
 
 
@@ -172,13 +172,16 @@ def load(path: str = LIB_PATH):
     lib.lbm_get_planes.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     lib.lbm_set_planes.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     lib.lbm_set_step_planes.argtypes = [H, ctypes.c_int, ctypes.c_int]
+    lib.lbm_step_begin.argtypes = [H, ctypes.c_int, ctypes.c_int]
+    lib.lbm_step_end.argtypes = [H]
     lib.lbm_crossing_bytes.argtypes = [H]
     lib.lbm_crossing_bytes.restype = ctypes.c_size_t
     lib.lbm_get_crossing.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     lib.lbm_set_crossing.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     for name in ("lbm_slab_plan", "lbm_slabs_create", "lbm_slabs_count", "lbm_slabs_init", "lbm_slabs_step",
                  "lbm_slabs_moments", "lbm_slabs_diagnostics", "lbm_slabs_sync", "lbm_get_planes",
-                 "lbm_set_planes", "lbm_set_step_planes", "lbm_get_crossing", "lbm_set_crossing"):
+                 "lbm_set_planes", "lbm_set_step_planes", "lbm_get_crossing", "lbm_set_crossing", "lbm_step_begin",
+                 "lbm_step_end"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_status",
                  "lbm_batch_set_budget", "lbm_batch_size", "lbm_batch_variants", "lbm_batch_set_variant",
@@ -407,6 +410,17 @@ def lbm_set_planes(h, first: int, count: int, buf):
 def lbm_set_step_planes(h, first: int, count: int):
     """Collide only planes [first, first + count) of the last axis (0: all)."""
     return _check(load().lbm_set_step_planes(h, int(first), int(count)))
+
+
+def lbm_step_begin(h, first: int, count: int):
+    """Collide planes [first, first + count) of the last axis as part of the
+    step the first call opens (its output becomes the current state)."""
+    return _check(load().lbm_step_begin(h, int(first), int(count)))
+
+
+def lbm_step_end(h):
+    """Close the step lbm_step_begin opened."""
+    return _check(load().lbm_step_end(h))
 
 
 def lbm_crossing_bytes(h) -> int:

@@ -2,21 +2,33 @@
 the last axis (``lbm_slab_plan``) and swaps halos with its neighbours through
 ``torch.distributed`` after every step.
 
-The plan, the halo depth and the exchange are the library's (``lbm_slab_plan``
-and the slab notes in include/lbm.h): the collision of a plane reads the
-populations of the two planes beyond it on either side, so a slab with two
-halo planes beyond each cut collides every plane it owns exactly and collides
-only those.  After a step its edge planes have pushed the populations that
-cross a cut into its halo planes; the swap moves them to the neighbour that
-owns their plane (round 1), then refreshes the halo planes from the
-neighbours' edge planes, which round 1 has completed (round 2).
+The plan and the halo depth are the library's (``lbm_slab_plan`` and the slab
+notes in include/lbm.h): the collision of a plane reads the populations of the
+two planes beyond it on either side, so a slab with two halo planes beyond
+each cut collides every plane it owns exactly and collides only those.  After
+a step its edge planes have pushed the populations that cross a cut into its
+halo planes.  The swap is one message per neighbour and direction: the
+crossing populations a slab pushed into its halo plane next to the cut, and
+its two edge planes.  The receiver
 
-``exchange_halos`` is the swap itself, written against callables that read
-and write planes and crossing populations of a slab, so that it does not care
-where they live.  ``SlabRank`` binds it to a library handle on this process's
-GPU: NCCL moves the device buffers; a gloo group gets them staged through host
-memory.  Only a process group is needed: the swap is point-to-point (no
-collective on the data path).
+1. writes the neighbour's edge planes into its halo planes;
+2. puts back, into the halo plane next to the cut, the crossing populations
+   it pushed there itself (the neighbour's copy of that plane lacks exactly
+   those; across a wall on x or y the wall column keeps the neighbour's value,
+   which ``lbm_set_crossing`` does);
+3. completes its own edge plane with the neighbour's crossing populations.
+
+Everything a rank sends comes from the planes next to its cuts, so
+``SlabRank`` steps those first (``lbm_step_begin``), posts the swap, steps
+its interior while the messages travel, and then applies what it received.
+
+``post_halos`` / ``finish_halos`` (and ``exchange_halos``, both in one call)
+are written against callables that read and write planes and crossing
+populations of a slab, so that they do not care where those live.
+``SlabRank`` binds them to a library handle on this process's GPU: NCCL
+moves the device buffers; a gloo group gets them staged through host memory.
+Only a process group is needed: the swap is point-to-point (no collective on
+the data path).
 """
 from __future__ import annotations
 
@@ -24,65 +36,78 @@ import numpy as np
 
 from . import lbm
 
-# tags of the messages a rank sends per step: crossing populations and edge
-# planes travelling up and down (with two slabs of a periodic domain both
-# directions go to the same peer)
-TAG_CROSS_UP, TAG_CROSS_DOWN, TAG_UP, TAG_DOWN = 0, 1, 2, 3
+# tags of the messages a rank sends per step, travelling up and down (with two
+# slabs of a periodic domain both directions go to the same peer)
+TAG_UP, TAG_DOWN = 2, 3
+# planes next to a cut stepped before the interior: the two edge planes the
+# swap sends take pushes from up to two planes beyond the cut
+EDGE_PLANES = 3
 
 
-def _swap(dist, group, sends, recvs):
-    """Post every send with every receive in one batch (no pair of ranks can
-    wait on each other) and wait for all of them."""
+def _pack(cross, planes):
+    import torch
+    return torch.cat([cross.reshape(-1), planes.reshape(-1)])
+
+
+def _unpack(buf, like_cross, like_planes):
+    n = like_cross.numel()
+    return buf[:n].reshape(like_cross.shape), buf[n:].reshape(like_planes.shape)
+
+
+def post_halos(dist, slab, get, get_cross, group=None):
+    """Read what this rank sends (``get(first, count)``: a contiguous tensor
+    of local planes [first, first + count); ``get_cross(plane, sign)``: the
+    populations of one plane whose velocity has last-axis component sign) and
+    post the sends and receives of one swap.  Returns the pending swap for
+    ``finish_halos``."""
+    H = lbm.LBM_SLAB_HALO
+    top, bottom = slab.lo + slab.own - 1, slab.lo      # edge planes
+    sends, recvs, todo = [], [], []
+    if slab.hi:   # up: my pushes into halo plane top + 1, my top edge planes
+        cross, planes = get_cross(top + 1, +1), get(top + 1 - H, H)
+        msg = _pack(cross, planes)
+        sends.append((msg, slab.above, TAG_UP))
+        buf = msg.new_empty(msg.shape)
+        recvs.append((buf, slab.above, TAG_DOWN))
+        todo.append(("up", buf, cross, planes))
+    if slab.lo:   # down: my pushes into halo plane bottom - 1, my bottom edge planes
+        cross, planes = get_cross(bottom - 1, -1), get(bottom, H)
+        msg = _pack(cross, planes)
+        sends.append((msg, slab.below, TAG_DOWN))
+        buf = msg.new_empty(msg.shape)
+        recvs.append((buf, slab.below, TAG_UP))
+        todo.append(("down", buf, cross, planes))
     ops = [dist.P2POp(dist.isend, t, peer, group, tag) for t, peer, tag in sends]
     ops += [dist.P2POp(dist.irecv, t, peer, group, tag) for t, peer, tag in recvs]
-    if ops:
-        for req in dist.batch_isend_irecv(ops):
-            req.wait()
+    reqs = dist.batch_isend_irecv(ops) if ops else []
+    return reqs, todo, sends
+
+
+def finish_halos(slab, pending, put, put_cross):
+    """Wait for the swap ``post_halos`` started and apply it
+    (``put(first, count, tensor)``, ``put_cross(plane, sign, tensor)``)."""
+    H = lbm.LBM_SLAB_HALO
+    reqs, todo, _ = pending
+    for req in reqs:
+        req.wait()
+    top, bottom = slab.lo + slab.own - 1, slab.lo
+    for side, buf, mine, like_planes in todo:
+        theirs, planes = _unpack(buf, mine, like_planes)
+        if side == "up":
+            put(top + 1, H, planes)        # the neighbour's lower edge planes
+            put_cross(top + 1, +1, mine)   # with my own pushes across the cut
+            put_cross(top, -1, theirs)     # its pushes complete my top plane
+        else:
+            put(0, H, planes)
+            put_cross(bottom - 1, -1, mine)
+            put_cross(bottom, +1, theirs)
 
 
 def exchange_halos(dist, slab, get, put, get_cross, put_cross, group=None):
     """Refresh the halos of `slab` (an ``lbm_slab``; this rank holds slab
-    index == rank) from its neighbours after a step.  ``get(first, count)``
-    returns a contiguous tensor of the local planes [first, first + count),
-    ``put(first, count, tensor)`` stores one; ``get_cross(plane, sign)`` and
-    ``put_cross(plane, sign, tensor)`` do the same for the populations of
-    one plane whose velocity has last-axis component ``sign``."""
-    H = lbm.LBM_SLAB_HALO
-    top, bottom = slab.lo + slab.own - 1, slab.lo      # edge planes
-    # round 1: what the edge planes pushed into the halo planes goes to its owner
-    sends, recvs, puts = [], [], []
-    if slab.hi:
-        sends.append((get_cross(top + 1, +1), slab.above, TAG_CROSS_UP))
-    if slab.lo:
-        sends.append((get_cross(bottom - 1, -1), slab.below, TAG_CROSS_DOWN))
-    if slab.lo:
-        buf = sends[-1][0].new_empty(sends[-1][0].shape)
-        recvs.append((buf, slab.below, TAG_CROSS_UP))
-        puts.append((bottom, +1, buf))
-    if slab.hi:
-        buf = sends[0][0].new_empty(sends[0][0].shape)
-        recvs.append((buf, slab.above, TAG_CROSS_DOWN))
-        puts.append((top, -1, buf))
-    _swap(dist, group, sends, recvs)
-    for plane, sign, buf in puts:
-        put_cross(plane, sign, buf)
-    # round 2: the halo planes from the neighbours' edge planes, now complete
-    sends, recvs, puts = [], [], []
-    if slab.hi:
-        sends.append((get(top + 1 - H, H), slab.above, TAG_UP))
-    if slab.lo:
-        sends.append((get(bottom, H), slab.below, TAG_DOWN))
-    if slab.lo:
-        buf = sends[-1][0].new_empty(sends[-1][0].shape)
-        recvs.append((buf, slab.below, TAG_UP))
-        puts.append((0, buf))
-    if slab.hi:
-        buf = sends[0][0].new_empty(sends[0][0].shape)
-        recvs.append((buf, slab.above, TAG_DOWN))
-        puts.append((top + 1, buf))
-    _swap(dist, group, sends, recvs)
-    for first, buf in puts:
-        put(first, H, buf)
+    index == rank) from its neighbours after a step: ``post_halos`` and
+    ``finish_halos`` in one call."""
+    finish_halos(slab, post_halos(dist, slab, get, get_cross, group), put, put_cross)
 
 
 def local_planes(field: np.ndarray, slab, axis: int, nm: int) -> np.ndarray:
@@ -95,9 +120,9 @@ def local_planes(field: np.ndarray, slab, axis: int, nm: int) -> np.ndarray:
 class SlabRank:
     """Slab ``rank`` of ``world`` of one domain on this process's GPU."""
 
-    def __init__(self, dist, group=None, **kw):
+    def __init__(self, dist, group=None, overlap: bool = True, **kw):
         import torch
-        self.dist, self.group = dist, group
+        self.dist, self.group, self.overlap = dist, group, overlap
         self.rank, self.world = dist.get_rank(group), dist.get_world_size(group)
         # the plane copies are enqueued on the handle's stream and the sends,
         # receives and buffer lifetimes are ordered on torch's current stream:
@@ -148,11 +173,39 @@ class SlabRank:
     def _put_cross(self, plane, sign, buf):
         lbm.lbm_set_crossing(self.h, plane, sign, buf)
 
+    def _ranges(self):
+        """(planes next to the cuts, interior planes) of the owned range, as
+        (first, count) pairs of local planes."""
+        sl, E = self.slab, EDGE_PLANES
+        if sl.own < 2 * E:
+            return [(sl.lo, sl.own)], []
+        edges = ([(sl.lo, E)] if sl.lo else []) + ([(sl.lo + sl.own - E, E)] if sl.hi else [])
+        lo, hi = sl.lo + (E if sl.lo else 0), sl.lo + sl.own - (E if sl.hi else 0)
+        return edges, ([(lo, hi - lo)] if hi > lo else [])
+
     def step(self, n: int = 1):
+        """n steps, each: the planes next to the cuts, the swap posted, the
+        interior planes while it travels, the swap applied (``overlap``);
+        otherwise, and with the three-launch step form, a whole step and
+        then the swap."""
+        if self.world == 1:
+            lbm.lbm_step(self.h, int(n))
+            return
+        if not self.overlap or self.params.step_kernel == lbm.LBM_STEP_THREE_LAUNCH:
+            for _ in range(int(n)):
+                lbm.lbm_step(self.h, 1)
+                exchange_halos(self.dist, self.slab, self._get, self._put, self._get_cross, self._put_cross,
+                               self.group)
+            return
+        edges, interior = self._ranges()
         for _ in range(int(n)):
-            lbm.lbm_step(self.h, 1)
-            exchange_halos(self.dist, self.slab, self._get, self._put, self._get_cross, self._put_cross,
-                           self.group)
+            for first, count in edges:
+                lbm.lbm_step_begin(self.h, first, count)
+            pending = post_halos(self.dist, self.slab, self._get, self._get_cross, self.group)
+            for first, count in interior:
+                lbm.lbm_step_begin(self.h, first, count)
+            finish_halos(self.slab, pending, self._put, self._put_cross)
+            lbm.lbm_step_end(self.h)
 
     def moments(self) -> dict:
         """rho, u*, T, P of the planes this rank owns (host arrays)."""

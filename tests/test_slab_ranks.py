@@ -2,13 +2,15 @@
 domain (the plan of lbm_slab_plan) with the FP64 oracle as the per-slab
 step, and swap halos with exchange_halos after every step.  The owned planes,
 put back together, must equal the undivided oracle run bit for bit: this
-checks the halo depth (two planes per cut), the two exchange rounds (the
-populations that cross a cut, then the halo planes), the neighbour and tag
-pairing of the swap, the periodic wrap and the treatment of the cut ends
-(fixed wall temperatures only at the domain's walls) independently of the
-GPU.  The oracle collides its halo planes too; their pushes across the cut
-are wrong (a halo plane lacks the planes beyond it), and round 1 must replace
-them: without it the run differs.  A rank that leaves between steps, or stays
+checks the halo depth (two planes per cut), the swap (one message per
+neighbour and direction: the populations that cross a cut and the two edge
+planes; the receiver restores its own crossing pushes into its halo plane and
+completes its edge plane with the neighbour's), the neighbour and tag pairing,
+the periodic wrap and the treatment of the cut ends (fixed wall temperatures
+only at the domain's walls) independently of the GPU.  The oracle collides its
+halo planes too; their pushes across the cut are wrong (a halo plane lacks the
+planes beyond it), and the crossing populations must replace them: without
+them the run differs.  A rank that leaves between steps, or stays
 but withholds its halo, makes its neighbour's swap fail (at once, or after
 the process group's timeout) instead of hanging."""
 import datetime
@@ -194,10 +196,10 @@ def test_slabs_on_gloo_ranks_equal_the_undivided_oracle_bit_for_bit(case):
 
 
 @pytest.mark.parametrize("case", ["d2q9_walls_3", "d3q19_periodic_3"])
-def test_without_the_crossing_round_the_slabs_differ(case):
-    """Negative control: the same runs with round 1 skipped (the halo planes'
-    own, incomplete pushes across the cut kept) do not reproduce the
-    undivided oracle."""
+def test_without_the_crossing_populations_the_slabs_differ(case):
+    """Negative control: the same runs without putting the crossing
+    populations (the edge planes keep the halo planes' own, incomplete pushes
+    across the cut) do not reproduce the undivided oracle."""
     sys.path.insert(0, ROOT)
     import oracle
     from paper_1705_10045_gb300 import lbm
@@ -247,10 +249,9 @@ def test_a_rank_that_withholds_its_halo_makes_the_swap_time_out():
 
 
 def test_whole_row_crossing_copies_break_walls_across_the_cut():
-    """Negative control for the wall rule of round 1: copying whole rows of
-    crossing populations overwrites what the receiving nodes' own
-    bounce-back at an x or y wall wrote, and the slabs no longer reproduce
-    the undivided oracle."""
+    """Negative control for the wall rule: putting whole rows of crossing
+    populations overwrites what a node's own bounce-back at an x or y wall
+    wrote, and the slabs no longer reproduce the undivided oracle."""
     sys.path.insert(0, ROOT)
     import oracle
     from paper_1705_10045_gb300 import lbm

@@ -253,50 +253,80 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
     // planes later, so its lines get the L2 evict-last hint.
     template <bool KEEP = false>
     __device__ __forceinline__ void m_node(int plane_off, int sp, int sr, int r) const {
-        const R third = R(1.0 / 3.0);
         {
             const int ra = r % RW, rb = r / RW;
             const size_t n = (size_t)(plane_off + ring_b[rb] + ring_a[ra]);
-            R fN[Q], fG[Q];
+            if constexpr (kSh) {
+                // shifted FP16 storage: the sums take the halves of the pair
+                // words directly (the same values as widening them first)
+                using H = Store<S, R>;
+                unsigned w[Q];
 #pragma unroll
-            for (int k = 0; k < Q; ++k)
-                if (KEEP && !COH && !kSh)
-                    Store<S, R>::load2_keep(src, pair_index(k, nn, n), R(V::w(k)) * p->rho_ref,
-                                            R(V::w(k)) * p->E_ref, fN[k], fG[k]);
-                else
-                    ld2(src, pair_index(k, nn, n), R(V::w(k)) * p->rho_ref, R(V::w(k)) * p->E_ref, fN[k], fG[k]);
-            // opposite directions k, k+1 pair up: their sum enters rho, their
-            // difference the momentum along c_k (each sum starts at its
-            // first term)
-            R rho = fN[0], ja = R(0), jb = R(0), jm = R(0), E = fG[0];
-            bool new_a = true, new_b = true, new_m = true;
+                for (int k = 0; k < Q; ++k)
+                    w[k] = COH ? H::word_coh(src, pair_index(k, nn, n)) : H::word(src, pair_index(k, nn, n));
+                R rho = H::lo(w[0]), ja = R(0), jb = R(0), jm = R(0), E = H::hi(w[0]);
+                bool new_a = true, new_b = true, new_m = true;
 #pragma unroll
-            for (int k = 1; k < Q; k += 2) {
-                const R s = fN[k] + fN[k + 1], d = fN[k] - fN[k + 1];
-                rho += s;
-                if (M::a(k) != 0) { const R t = M::a(k) > 0 ? d : -d; ja = new_a ? t : ja + t; new_a = false; }
-                if (M::b(k) != 0) { const R t = M::b(k) > 0 ? d : -d; jb = new_b ? t : jb + t; new_b = false; }
-                if (M::m(k) != 0) { const R t = M::m(k) > 0 ? d : -d; jm = new_m ? t : jm + t; new_m = false; }
-            }
+                for (int k = 1; k < Q; k += 2) {
+                    const R x = H::lo(w[k]);
+                    const R s = H::add_lo(w[k + 1], x), dn = H::sub_lo(w[k + 1], x);   // x + y and y - x
+                    rho += s;
+                    if (M::a(k) != 0) { const R t = M::a(k) > 0 ? -dn : dn; ja = new_a ? t : ja + t; new_a = false; }
+                    if (M::b(k) != 0) { const R t = M::b(k) > 0 ? -dn : dn; jb = new_b ? t : jb + t; new_b = false; }
+                    if (M::m(k) != 0) { const R t = M::m(k) > 0 ? -dn : dn; jm = new_m ? t : jm + t; new_m = false; }
+                }
 #pragma unroll
-            for (int k = 1; k < Q; ++k) E += fG[k];
-            if constexpr (kSh) {   // sums of shifted values: sum_k w_k = 1, sum_k w_k c_k = 0
+                for (int k = 1; k < Q; ++k) E = H::add_hi(w[k], E);
+                // sums of shifted values: sum_k w_k = 1, sum_k w_k c_k = 0
                 rho += p->rho_ref;
                 E += p->E_ref;
+                m_finish(sp, sr, r, rho, ja, jb, jm, E);
+                return;
+            } else {
+                R fN[Q], fG[Q];
+#pragma unroll
+                for (int k = 0; k < Q; ++k)
+                    if (KEEP && !COH)
+                        Store<S, R>::load2_keep(src, pair_index(k, nn, n), R(V::w(k)) * p->rho_ref,
+                                                R(V::w(k)) * p->E_ref, fN[k], fG[k]);
+                    else
+                        ld2(src, pair_index(k, nn, n), R(V::w(k)) * p->rho_ref, R(V::w(k)) * p->E_ref, fN[k], fG[k]);
+                // opposite directions k, k+1 pair up: their sum enters rho, their
+                // difference the momentum along c_k (each sum starts at its
+                // first term)
+                R rho = fN[0], ja = R(0), jb = R(0), jm = R(0), E = fG[0];
+                bool new_a = true, new_b = true, new_m = true;
+#pragma unroll
+                for (int k = 1; k < Q; k += 2) {
+                    const R s = fN[k] + fN[k + 1], d = fN[k] - fN[k + 1];
+                    rho += s;
+                    if (M::a(k) != 0) { const R t = M::a(k) > 0 ? d : -d; ja = new_a ? t : ja + t; new_a = false; }
+                    if (M::b(k) != 0) { const R t = M::b(k) > 0 ? d : -d; jb = new_b ? t : jb + t; new_b = false; }
+                    if (M::m(k) != 0) { const R t = M::m(k) > 0 ? d : -d; jm = new_m ? t : jm + t; new_m = false; }
+                }
+#pragma unroll
+                for (int k = 1; k < Q; ++k) E += fG[k];
+                m_finish(sp, sr, r, rho, ja, jb, jm, E);
             }
-            const R T = E / (rho * p->c_v);
-            const R U = fma(-rho, third, eos_pressure(*p, rho, T));
-            phi(sp, r) = U < R(0) ? sqrt(-U) : R(0);
-            const int fa = ra - 1, fb = rb - (RB - FB);
-            if (fa >= 0 && fa < FW && fb >= 0 && fb < Sh::FH) {
-                const int f = fb * FW + fa;
-                const R inv_rho = R(1) / rho;
-                rut(sr, 0, f) = rho;
-                rut(sr, 1, f) = ja * inv_rho;
-                rut(sr, 2, f) = jb * inv_rho;
-                rut(sr, 3, f) = jm * inv_rho;
-                rut(sr, 4, f) = T;
-            }
+        }
+    }
+    // Phi of ring node r from its moments, and rho, u, T if r lies in the
+    // 1-ring region
+    __device__ __forceinline__ void m_finish(int sp, int sr, int r, R rho, R ja, R jb, R jm, R E) const {
+        const R third = R(1.0 / 3.0);
+        const int ra = r % RW, rb = r / RW;
+        const R T = E / (rho * p->c_v);
+        const R U = fma(-rho, third, eos_pressure(*p, rho, T));
+        phi(sp, r) = U < R(0) ? sqrt(-U) : R(0);
+        const int fa = ra - 1, fb = rb - (RB - FB);
+        if (fa >= 0 && fa < FW && fb >= 0 && fb < Sh::FH) {
+            const int f = fb * FW + fa;
+            const R inv_rho = R(1) / rho;
+            rut(sr, 0, f) = rho;
+            rut(sr, 1, f) = ja * inv_rho;
+            rut(sr, 2, f) = jb * inv_rho;
+            rut(sr, 3, f) = jm * inv_rho;
+            rut(sr, 4, f) = T;
         }
     }
 
@@ -437,9 +467,14 @@ template <int Q, typename S, typename R, int TX, int TY, bool COH = false, bool 
         if (fma(-rho, third, P) >= R(0)) atomicAdd(&cnt->clamps, 1ull);
 
         R E = hvk(0);
+        if constexpr (kSh) {
 #pragma unroll
-        for (int k = 1; k < Q; ++k) E += hvk(k);
-        if constexpr (kSh) E += p->E_ref;
+            for (int k = 1; k < Q; ++k) E = Store<S, R>::add_hi(wv[k], E);
+            E += p->E_ref;
+        } else {
+#pragma unroll
+            for (int k = 1; k < Q; ++k) E += hvk(k);
+        }
         if (!(finite_pos(rho) && finite_pos(E))) atomicAdd(&cnt->bad, 1ull);
         const R dEoverE = dE / E;
         // node offsets of x + c_k: +-1 along a and b (periodic), along the

@@ -237,6 +237,26 @@ template <> struct Store<__half, float> {
         unpack(word_last_coh(p, i), sN, sG, a, b);
     }
     __device__ static void load2_raw(const __half* p, size_t i, float& a, float& b) { unpack_raw(word(p, i), a, b); }
+    // the halves of a pair word widened, and sums with one half rounded once in
+    // FP32 (mixed-precision add / sub: a half widens to FP32 exactly, so these
+    // equal widening first, in one instruction fewer)
+    __device__ static float lo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))); }
+    __device__ static float hi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+    __device__ static float add_lo(unsigned w, float acc) {   // acc + N half
+        float r;
+        asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"((unsigned short)(w & 0xFFFFu)), "f"(acc));
+        return r;
+    }
+    __device__ static float add_hi(unsigned w, float acc) {   // acc + g half
+        float r;
+        asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"((unsigned short)(w >> 16)), "f"(acc));
+        return r;
+    }
+    __device__ static float sub_lo(unsigned w, float acc) {   // N half - acc
+        float r;
+        asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"((unsigned short)(w & 0xFFFFu)), "f"(acc));
+        return r;
+    }
     __device__ static void load2_last_raw(const __half* p, size_t i, float& a, float& b) {
         unpack_raw(word_last(p, i), a, b);
     }

@@ -309,11 +309,17 @@ void lbm_batch_destroy(lbm_batch* b);
  * each cut every plane a slab owns is collided exactly.  A slab collides its
  * owned planes only (lbm_set_step_planes); its edge planes push the
  * populations that cross a cut into its halo planes.  The swap after each
- * step has two rounds: (1) the crossing populations of each cut (the
+ * step does two things: (1) the crossing populations of each cut (the
  * directions whose velocity points across it, 5 for D3Q19 and 3 for D2Q9;
  * lbm_get_crossing / lbm_set_crossing) move from the pushing slab's halo
  * plane to the owning slab's edge plane; (2) each slab's halo planes are
- * overwritten with its neighbours' edge planes, complete after round 1.
+ * overwritten with its neighbours' edge planes, complete after (1).  On one
+ * GPU (lbm_slabs_*) these are two phases of device copies.  Between
+ * processes they fit in one message per neighbour and direction: the
+ * crossing populations and the two edge planes, where the receiver restores
+ * its own crossing populations into the halo plane next to the cut (the
+ * Python binding's SlabRank; with lbm_step_begin the planes next to the cuts
+ * step first and the messages travel while the interior steps).
  * FP64 and FP32 slabs reproduce the undivided domain bit for bit; FP16 slabs
  * key their stochastic rounding by node index within the slab, so they agree
  * in distribution, not in bits. */
@@ -411,8 +417,9 @@ int lbm_set_step_planes(lbm_handle* h, int first, int count);
  * closes the step.  A range stepped this way writes exactly what lbm_step
  * writes for those planes, so ranges that cover [0, nm) (or the range of
  * lbm_set_step_planes) reproduce lbm_step bit for bit.  While a step is open,
- * lbm_step, lbm_profile_step, lbm_init and lbm_set_state refuse
- * (LBM_ERR_INVALID_ARG).  Errors (LBM_ERR_INVALID_ARG): null handle, no state
+ * lbm_step, lbm_profile_step, lbm_init, lbm_set_state, lbm_get_state and
+ * lbm_moments_f refuse (LBM_ERR_INVALID_ARG; the last two use the idle
+ * population buffer, which is the open step's input).  Errors (LBM_ERR_INVALID_ARG): null handle, no state
  * yet, a range outside the last axis, the three-launch step form; lbm_step_end
  * with no open step. */
 int lbm_step_begin(lbm_handle* h, int first, int count);

@@ -427,6 +427,7 @@ int lbm_moments_f(lbm_handle* h, float* rho, float* u, float* T, float* P, int m
     lbm::TraceRange trace_("lbm_moments_f");
     if (int rc = check_handle(h)) return rc;
     if (int rc = need_init(h)) return rc;
+    if (int rc = no_pending(h, "lbm_moments_f")) return rc;   // host output stages in the idle buffer
     if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) {
         set_error("lbm_moments_f: bad mem flag");
         return LBM_ERR_INVALID_ARG;
@@ -498,6 +499,7 @@ int lbm_get_state(lbm_handle* h, void* buf, int mem) {
     lbm::TraceRange trace_("lbm_get_state");
     if (int rc = check_handle(h)) return rc;
     if (int rc = need_init(h)) return rc;
+    if (int rc = no_pending(h, "lbm_get_state")) return rc;   // converts in the idle buffer
     if (!buf || (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE)) {
         set_error("lbm_get_state: null buffer or bad mem flag");
         return LBM_ERR_INVALID_ARG;

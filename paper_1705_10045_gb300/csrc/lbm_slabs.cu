@@ -152,9 +152,10 @@ int copy_table(const void* src, void* dst, const RowTable& t, int rows, long lon
 // arrives at a cut's edge plane moving away from a wall on x (or on y of
 // D3Q19) would come from a node beyond that wall: no slab pushes it.  The
 // receiving node's own bounce-back wrote it in the receiving slab's step, and
-// the pushing slab's halo slot holds no value of this step.  So round 1 skips,
-// per direction, the column x = 0 (c_x = +1) or x = nx - 1 (c_x = -1) across
-// a wall on x, and the row y = 0 or ny - 1 across a wall on y.  -1: no skip.
+// the pushing slab's halo slot holds no value of this step.  So the crossing
+// copy skips, per direction, the column x = 0 (c_x = +1) or x = nx - 1
+// (c_x = -1) across a wall on x, and the row y = 0 or ny - 1 across a wall on
+// y.  -1: no skip.
 struct CrossSkip {
     int x[8], y[8];
 };

@@ -64,7 +64,8 @@ def test_an_open_step_exposes_its_output_and_blocks_other_steps():
         lbm.lbm_get_planes(sim.h, 15, 1, got)  # the open step's output
         assert np.array_equal(got, want)
         for call in (lambda: lbm.lbm_step(sim.h, 1), lambda: lbm.lbm_profile_step(sim.h, 1),
-                     lambda: sim.init(f.rho, np.ascontiguousarray(f.u), 1.5 * f.T)):
+                     lambda: sim.init(f.rho, np.ascontiguousarray(f.u), 1.5 * f.T), lambda: sim.get_state(),
+                     lambda: lbm.lbm_moments_f(sim.h)):
             with pytest.raises(lbm.LbmError) as e:
                 call()
             assert e.value.code == lbm.LBM_ERR_INVALID_ARG

@@ -120,7 +120,7 @@ def _rank(rank, world, port, case, out, leave_after, withhold_at=None, timeout_s
         # in-plane axes of a plane slice (Q, ny, nx) for D3Q19, (Q, nx) for D2Q9,
         # with their walls: a crossing population that would come from beyond
         # such a wall is not pushed by the neighbour; the receiving node's own
-        # bounce-back wrote it, so round 1 must leave it alone
+        # bounce-back wrote it, so the crossing put must leave it alone
         walls = [(0, whole.wall_x, -1)] + ([(1, whole.wall_y, -2)] if Q == 19 else [])
 
         def get_cross(plane, sgn):

@@ -382,6 +382,7 @@ int lbm_step_begin(lbm_handle* h, int first, int count) {
 }
 
 int lbm_step_end(lbm_handle* h) {
+    lbm::TraceRange trace_("lbm_step_end");
     if (int rc = check_handle(h)) return rc;
     if (!h->pending) {
         set_error("lbm_step_end: no step is open");

@@ -343,7 +343,9 @@ def slabs_leg(count: int, steps: int, rho_h, u_h, eps_h, stream, dev) -> dict:
     return {"slabs": count, "value": nn / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": steps,
             "halo_planes_held": sum(p.lo + p.hi for p in plans), "halo_planes_collided": 0,
             "bytes_copied_per_step": sides * (lbm.LBM_SLAB_HALO * plane_bytes + crossing_bytes),
-            "launches_per_step": count + 2 * sides, "bad_nodes": diag["bad"]}
+            # the slabs' fused steps, then one launch per phase of the swap
+            # (crossing populations, halo planes) for all cuts together
+            "launches_per_step": count + (2 if count > 1 else 0), "bad_nodes": diag["bad"]}
 
 
 D2Q9_NX, D2Q9_NY = 8192, 4608

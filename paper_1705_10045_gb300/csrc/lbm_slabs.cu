@@ -211,34 +211,6 @@ int copy_crossing_rows(const void* src, void* dst, const RowTable& t, const Cros
     return cuda_error(cudaGetLastError(), "crossing copy launch");
 }
 
-// the crossing populations `sign` of plane sp of src's current state into
-// plane dp of dst's (walls across the plane: the wall skips above)
-int copy_crossing(lbm_handle* dst, int dp, const lbm_handle* src, int sp, int sign, cudaStream_t stream) {
-    int ks[8];
-    const int n = crossing_dirs(src->Q, sign, ks);
-    const long long plane = plane_nodes(src->p), e = 2 * (long long)src->elem;
-    RowTable t;
-    for (int j = 0; j < n; ++j) {
-        t.src[j] = (ks[j] * src->nn + sp * plane) * e;
-        t.dst[j] = (ks[j] * dst->nn + dp * plane) * e;
-    }
-    CrossSkip sk;
-    if (crossing_skips(dst->p, ks, n, sk))
-        return copy_crossing_rows(src->pop[src->cur], dst->pop[dst->cur], t, sk, n, plane, dst->p.nx, dst->elem,
-                                  stream);
-    return copy_table(src->pop[src->cur], dst->pop[dst->cur], t, n, plane * e, stream);
-}
-
-// planes [first, first + count) of every population array of the current state
-// (Q arrays of node pairs (N_k, g_k), 2 elem bytes per node)
-int copy_planes(lbm_handle* dst, int dst_first, const lbm_handle* src, int src_first, int count,
-                cudaStream_t stream) {
-    const long long plane = plane_nodes(src->p);
-    const long long e = 2 * (long long)src->elem;
-    const auto* s = static_cast<const unsigned char*>(src->pop[src->cur]) + src_first * plane * e;
-    auto* d = static_cast<unsigned char*>(dst->pop[dst->cur]) + dst_first * plane * e;
-    return copy_rows(s, src->nn * e, d, dst->nn * e, count * plane * e, src->Q, stream);
-}
 
 // Conservation sums of nodes [i0, i0 + n) of a population buffer whose
 // arrays are nn apart: per-thread compensated sums in the arithmetic type,
@@ -336,36 +308,137 @@ int check_slabs(const lbm_slabs* s) {
     return LBM_OK;
 }
 
-// the two rounds of the exchange (see the top of this file), on `stream`
-int exchange(lbm_slabs* s, cudaStream_t stream) {
-    const int H = LBM_SLAB_HALO;
-    // (1) crossing populations: slab i's upper edge plane pushed them into its
-    // halo plane lo + own, its lower edge plane into lo - 1
-    for (int i = 0; i < s->count; ++i) {
-        const lbm_slab& a = s->plan[i];
-        if (a.hi) {
-            const lbm_slab& b = s->plan[a.above];
-            if (int rc = copy_crossing(s->h[a.above], b.lo, s->h[i], a.lo + a.own, +1, stream)) return rc;
-        }
-        if (a.lo) {
-            const lbm_slab& b = s->plan[a.below];
-            if (int rc = copy_crossing(s->h[a.below], b.lo + b.own - 1, s->h[i], a.lo - 1, -1, stream))
-                return rc;
-        }
+// Rows of one exchange phase for one launch: absolute row addresses (every
+// row of a phase has the same length) and, for crossing rows, the wall
+// column and row the receiver keeps (-1: none).  At most kListRows rows per
+// launch (3.8 KB of kernel parameters); longer lists take several launches.
+constexpr int kListRows = 150;
+struct RowList {
+    unsigned long long src[kListRows], dst[kListRows];
+    short skip_x[kListRows], skip_y[kListRows];
+};
+
+// crossing rows: node pairs P of a plane, all but the wall column and row
+template <typename P>
+__global__ void __launch_bounds__(256) crossing_list_kernel(RowList t, long long plane, int nx) {
+    const P* s = reinterpret_cast<const P*>(t.src[blockIdx.y]);
+    P* d = reinterpret_cast<P*>(t.dst[blockIdx.y]);
+    const int sx = t.skip_x[blockIdx.y];
+    const long long sy = t.skip_y[blockIdx.y];
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < plane;
+         n += (long long)gridDim.x * blockDim.x) {
+        const long long y = n / nx;
+        if ((int)(n - y * nx) == sx || y == sy) continue;
+        d[n] = s[n];
     }
-    // (2) halo planes from the neighbours' edge planes, now complete
-    for (int i = 0; i < s->count; ++i) {
-        const lbm_slab& a = s->plan[i];
-        if (a.hi) {
-            const lbm_slab& b = s->plan[a.above];
-            if (int rc = copy_planes(s->h[i], a.lo + a.own, s->h[a.above], b.lo, H, stream)) return rc;
+}
+
+// plain rows of `words` words W
+template <typename W>
+__global__ void __launch_bounds__(256) rows_list_kernel(RowList t, long long words) {
+    const W* s = reinterpret_cast<const W*>(t.src[blockIdx.y]);
+    W* d = reinterpret_cast<W*>(t.dst[blockIdx.y]);
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (long long)gridDim.x * blockDim.x)
+        d[w] = s[w];
+}
+
+// one phase of the exchange: `rows` rows of `bytes` bytes each, crossing rows
+// (pair granularity, wall skips; pair = 2 elem bytes) or plain rows (the
+// widest word that divides every address and the length)
+int launch_list(const std::vector<unsigned long long>& src, const std::vector<unsigned long long>& dst,
+                const std::vector<short>& skx, const std::vector<short>& sky, long long bytes, bool crossing,
+                long long plane, int nx, int elem, cudaStream_t stream) {
+    const int n = (int)src.size();
+    for (int r0 = 0; r0 < n; r0 += kListRows) {
+        const int rows = n - r0 < kListRows ? n - r0 : kListRows;
+        RowList t;
+        unsigned long long all = (unsigned long long)bytes;
+        for (int r = 0; r < rows; ++r) {
+            t.src[r] = src[r0 + r];
+            t.dst[r] = dst[r0 + r];
+            t.skip_x[r] = skx[r0 + r];
+            t.skip_y[r] = sky[r0 + r];
+            all |= t.src[r] | t.dst[r];
         }
-        if (a.lo) {
-            const lbm_slab& b = s->plan[a.below];
-            if (int rc = copy_planes(s->h[i], 0, s->h[a.below], b.lo + b.own - H, H, stream)) return rc;
+        if (crossing) {
+            long long bx = (plane + 255) / 256;
+            if (bx > 512) bx = 512;
+            const dim3 grid((unsigned)bx, (unsigned)rows);
+            switch (2 * elem) {
+                case 16: crossing_list_kernel<uint4><<<grid, 256, 0, stream>>>(t, plane, nx); break;
+                case 8: crossing_list_kernel<unsigned long long><<<grid, 256, 0, stream>>>(t, plane, nx); break;
+                default: crossing_list_kernel<unsigned><<<grid, 256, 0, stream>>>(t, plane, nx); break;
+            }
+        } else {
+            const int wb = (all & 15) == 0 ? 16 : (all & 7) == 0 ? 8 : (all & 3) == 0 ? 4 : 2;
+            const long long words = bytes / wb;
+            long long bx = (words + 255) / 256;
+            if (bx > 512) bx = 512;
+            const dim3 grid((unsigned)bx, (unsigned)rows);
+            switch (wb) {
+                case 16: rows_list_kernel<uint4><<<grid, 256, 0, stream>>>(t, words); break;
+                case 8: rows_list_kernel<unsigned long long><<<grid, 256, 0, stream>>>(t, words); break;
+                case 4: rows_list_kernel<unsigned><<<grid, 256, 0, stream>>>(t, words); break;
+                default: rows_list_kernel<unsigned short><<<grid, 256, 0, stream>>>(t, words); break;
+            }
         }
+        if (int rc = cuda_error(cudaGetLastError(), "exchange launch")) return rc;
     }
     return LBM_OK;
+}
+
+// the two phases of the exchange (see the top of this file), on `stream`,
+// one launch each: every slab's rows go into one list
+int exchange(lbm_slabs* s, cudaStream_t stream) {
+    const int H = LBM_SLAB_HALO;
+    const long long plane = plane_nodes(s->p);
+    const int elem = (int)s->h[0]->elem;
+    const long long e = 2 * (long long)elem;
+    auto base = [&](int i) { return (unsigned long long)(size_t)s->h[i]->pop[s->h[i]->cur]; };
+    std::vector<unsigned long long> src, dst;
+    std::vector<short> skx, sky;
+    // (1) crossing populations: slab i's upper edge plane pushed them into its
+    // halo plane lo + own, its lower edge plane into lo - 1; they go to the
+    // neighbour's edge plane (wall columns and rows of the receiver skipped)
+    for (int i = 0; i < s->count; ++i) {
+        const lbm_slab& a = s->plan[i];
+        for (int sign = 1; sign >= -1; sign -= 2) {
+            if (sign > 0 ? !a.hi : !a.lo) continue;
+            const int j = sign > 0 ? a.above : a.below;
+            const lbm_slab& b = s->plan[j];
+            const int sp = sign > 0 ? a.lo + a.own : a.lo - 1, dp = sign > 0 ? b.lo : b.lo + b.own - 1;
+            int ks[8];
+            const int n = crossing_dirs(s->h[i]->Q, sign, ks);
+            CrossSkip sk;
+            crossing_skips(s->h[j]->p, ks, n, sk);
+            for (int r = 0; r < n; ++r) {
+                src.push_back(base(i) + (unsigned long long)((ks[r] * s->h[i]->nn + sp * plane) * e));
+                dst.push_back(base(j) + (unsigned long long)((ks[r] * s->h[j]->nn + dp * plane) * e));
+                skx.push_back((short)sk.x[r]);
+                sky.push_back((short)sk.y[r]);
+            }
+        }
+    }
+    if (int rc = launch_list(src, dst, skx, sky, plane * e, true, plane, s->p.nx, elem, stream)) return rc;
+    // (2) halo planes from the neighbours' edge planes, now complete: per
+    // side Q rows of H planes
+    src.clear(); dst.clear(); skx.clear(); sky.clear();
+    for (int i = 0; i < s->count; ++i) {
+        const lbm_slab& a = s->plan[i];
+        for (int sign = 1; sign >= -1; sign -= 2) {
+            if (sign > 0 ? !a.hi : !a.lo) continue;
+            const int j = sign > 0 ? a.above : a.below;
+            const lbm_slab& b = s->plan[j];
+            const int first_a = sign > 0 ? a.lo + a.own : 0, first_b = sign > 0 ? b.lo : b.lo + b.own - H;
+            for (int k = 0; k < s->h[i]->Q; ++k) {
+                dst.push_back(base(i) + (unsigned long long)((k * s->h[i]->nn + first_a * plane) * e));
+                src.push_back(base(j) + (unsigned long long)((k * s->h[j]->nn + first_b * plane) * e));
+                skx.push_back(-1);
+                sky.push_back(-1);
+            }
+        }
+    }
+    return launch_list(src, dst, skx, sky, H * plane * e, false, plane, s->p.nx, elem, stream);
 }
 
 }  // namespace

@@ -110,6 +110,19 @@ def exchange_halos(dist, slab, get, put, get_cross, put_cross, group=None):
     finish_halos(slab, post_halos(dist, slab, get, get_cross, group), put, put_cross)
 
 
+def split_ranges(slab, edge: int = EDGE_PLANES):
+    """(planes next to the cuts, interior planes) of the planes `slab` owns,
+    as lists of (first, count) local plane ranges: `edge` planes beside each
+    cut (a slab ending at a wall has no cut there), the rest in one range.
+    A slab too thin to split steps all its owned planes in the first list."""
+    sl, E = slab, edge
+    if sl.own < 2 * E:
+        return [(sl.lo, sl.own)], []
+    edges = ([(sl.lo, E)] if sl.lo else []) + ([(sl.lo + sl.own - E, E)] if sl.hi else [])
+    lo, hi = sl.lo + (E if sl.lo else 0), sl.lo + sl.own - (E if sl.hi else 0)
+    return edges, ([(lo, hi - lo)] if hi > lo else [])
+
+
 def local_planes(field: np.ndarray, slab, axis: int, nm: int) -> np.ndarray:
     """The slab's local planes (halos included) of a whole-domain field along
     `axis`, wrapping around a periodic last axis."""
@@ -174,14 +187,7 @@ class SlabRank:
         lbm.lbm_set_crossing(self.h, plane, sign, buf)
 
     def _ranges(self):
-        """(planes next to the cuts, interior planes) of the owned range, as
-        (first, count) pairs of local planes."""
-        sl, E = self.slab, EDGE_PLANES
-        if sl.own < 2 * E:
-            return [(sl.lo, sl.own)], []
-        edges = ([(sl.lo, E)] if sl.lo else []) + ([(sl.lo + sl.own - E, E)] if sl.hi else [])
-        lo, hi = sl.lo + (E if sl.lo else 0), sl.lo + sl.own - (E if sl.hi else 0)
-        return edges, ([(lo, hi - lo)] if hi > lo else [])
+        return split_ranges(self.slab)
 
     def step(self, n: int = 1):
         """n steps, each: the planes next to the cuts, the swap posted, the

@@ -79,3 +79,31 @@ def test_slabs_create_rejects_bad_counts_before_touching_a_device(count):
     s = ctypes.c_void_p()
     assert lbm.load().lbm_slabs_create(ctypes.byref(p), count, ctypes.byref(s)) == lbm.LBM_ERR_INVALID_ARG
     assert not s.value
+
+
+@pytest.mark.parametrize("lattice,nm,wall", [(19, 256, 1), (19, 17, 0), (9, 60, 0), (19, 40, 1), (9, 33, 1)])
+@pytest.mark.parametrize("count", [1, 2, 3, 4, 5])
+def test_split_ranges_cover_the_owned_planes_once_with_the_cut_planes_first(lattice, nm, wall, count):
+    """The planes a slab process steps before posting its swap and those it
+    steps while the swap travels: disjoint, covering its owned planes, and
+    the first list holds the three planes beside every cut (which give the
+    two edge planes the swap sends all their pushes)."""
+    from paper_1705_10045_gb300.slabs import EDGE_PLANES, split_ranges
+    kw = dict(lattice=lattice, nx=8, ny=nm if lattice == 9 else 6, nz=nm if lattice == 19 else 1, wall=wall)
+    p = lbm.make_params(**kw)
+    if count > 1 and nm // count < lbm.LBM_SLAB_HALO:
+        return
+    for i in range(count):
+        sl = lbm.lbm_slab_plan(p, count, i)
+        edges, interior = split_ranges(sl)
+        planes = [q for f, c in edges + interior for q in range(f, f + c)]
+        assert sorted(planes) == list(range(sl.lo, sl.lo + sl.own))
+        assert len(planes) == len(set(planes))
+        first = {q for f, c in edges for q in range(f, f + c)}
+        need = set()
+        if sl.lo:
+            need |= set(range(sl.lo, min(sl.lo + EDGE_PLANES, sl.lo + sl.own)))
+        if sl.hi:
+            need |= set(range(max(sl.lo, sl.lo + sl.own - EDGE_PLANES), sl.lo + sl.own))
+        assert need <= first
+        assert all(c >= 1 for _, c in edges + interior)
